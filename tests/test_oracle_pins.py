@@ -1,0 +1,319 @@
+"""Pins for the CPU oracle against things other than itself.
+
+Each test fixes the oracle to a value that the paper's definitions or the
+mathematics determine independently:
+
+* hand-derived cut capacities and minimum cuts (tests/golden/tiny_cuts.json,
+  Sec. 2.1 definitions);
+* closed forms of lambda for K_n, C_n, trees, two cliques joined by k
+  disjoint edges, disconnected graphs;
+* brute-force enumeration (definition of lambda, Sec. 2.1) against
+  Stoer-Wagner and NOI on thousands of random tiny graphs;
+* Lemma 1 (capped queue) -- capped and uncapped NOI agree;
+* contraction (Sec. 2.1) preserves the capacity of every cut that keeps each
+  block on one side;
+* the published splitmix64 output sequence for seed 1234567.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def side_ok(side, n):
+    s = np.asarray(side)
+    return len(s) == n and s[0] == 0 and 0 < s.sum() < n
+
+
+def test_splitmix64_published_sequence():
+    # Vigna's reference splitmix64: state advances by the golden gamma and each
+    # output is the finaliser of the new state; seed 1234567 gives these five.
+    expected = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                4593380528125082431, 16408922859458223821]
+    state = 1234567
+    got = []
+    for _ in range(5):
+        got.append(oracle.splitmix64(state))
+        state = (state + 0x9E3779B97F4A7C15) % 2**64
+    assert got == expected
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(GOLDEN, "tiny_cuts.json")))["cases"],
+                         ids=lambda c: c["name"])
+def test_golden_tiny_cuts(case):
+    n = case["n"]
+    e = np.array(case["edges"])
+    g = graphgen.from_edges(n, e[:, 0], e[:, 1], e[:, 2])
+    side = np.zeros(n, dtype=np.uint8)
+    side[case["side"]] = 1
+    assert oracle.cut_weight(*g, side) == case["side_capacity"]
+    assert oracle.cut_weight(*g, 1 - side) == case["side_capacity"]
+    for algo in (oracle.brute_force, oracle.stoer_wagner):
+        lam, s = algo(*g)
+        assert lam == case["lambda"]
+        assert side_ok(s, n) and oracle.cut_weight(*g, s) == lam
+    lam, s, _ = oracle.noi(*g)
+    assert lam == case["lambda"] and oracle.cut_weight(*g, s) == lam
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 8, 11])
+@pytest.mark.parametrize("wt", [1, 7])
+def test_complete_graph(n, wt):
+    g = graphgen.complete(n, wt)
+    expect = (n - 1) * wt
+    assert oracle.brute_force(*g)[0] == expect
+    assert oracle.stoer_wagner(*g)[0] == expect
+    assert oracle.noi(*g)[0] == expect
+    assert oracle.noi(*g, capped=False)[0] == expect
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 16])
+@pytest.mark.parametrize("wt", [1, 5])
+def test_cycle(n, wt):
+    g = graphgen.cycle(n, wt)
+    expect = 2 * wt
+    if n <= 20:
+        assert oracle.brute_force(*g)[0] == expect
+    assert oracle.stoer_wagner(*g)[0] == expect
+    assert oracle.noi(*g)[0] == expect
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tree_is_min_edge(seed):
+    g = graphgen.random_tree(14, seed)
+    expect = int(g[2].min())
+    assert oracle.brute_force(*g)[0] == expect
+    assert oracle.stoer_wagner(*g)[0] == expect
+    lam, side, _ = oracle.noi(*g)
+    assert lam == expect and oracle.cut_weight(*g, side) == expect
+
+
+@pytest.mark.parametrize("a,k", [(5, 1), (6, 3), (8, 2), (30, 5)])
+def test_two_cliques(a, k):
+    g = graphgen.two_cliques(a, k, seed=a + k)
+    if 2 * a <= 20:
+        assert oracle.brute_force(*g)[0] == k
+    lam, side = oracle.stoer_wagner(*g)
+    assert lam == k
+    # the only cut of weight k separates the cliques
+    assert side[:a].sum() in (0, a) and side[a:].sum() in (0, a)
+    assert oracle.noi(*g)[0] == k
+
+
+def test_disconnected_is_zero():
+    u = np.array([0, 1, 3, 4])
+    v = np.array([1, 2, 4, 5])
+    g = graphgen.from_edges(6, u, v, np.array([3, 4, 5, 6]))
+    assert oracle.brute_force(*g)[0] == 0
+    lam, side = oracle.stoer_wagner(*g)
+    assert lam == 0 and oracle.cut_weight(*g, side) == 0
+    lam, side, _ = oracle.noi(*g)
+    assert lam == 0 and oracle.cut_weight(*g, side) == 0 and side_ok(side, 6)
+
+
+def test_isolated_vertex_is_zero():
+    g = graphgen.from_edges(4, np.array([0, 1]), np.array([1, 2]))
+    assert oracle.brute_force(*g)[0] == 0
+    assert oracle.stoer_wagner(*g)[0] == 0
+    assert oracle.noi(*g)[0] == 0
+
+
+def _random_tiny(rng, i):
+    n = int(rng.integers(2, 15))
+    kind = i % 4
+    if kind == 0:
+        g = graphgen.random_gnp(n, float(rng.uniform(0.15, 0.9)), seed=i, wmax=100)
+    elif kind == 1:
+        g = graphgen.random_gnp(n, float(rng.uniform(0.3, 1.0)), seed=i, wmax=3)
+    elif kind == 2:
+        g = graphgen.random_connected(n, int(rng.integers(0, 3 * n)), seed=i, wmax=10)
+    else:
+        # parallel arcs and self-loops in the input
+        m = int(rng.integers(1, 3 * n))
+        u = rng.integers(0, n, size=m)
+        v = rng.integers(0, n, size=m)
+        g = graphgen.from_edges(n, u, v, rng.integers(1, 6, size=m))
+    return n, g
+
+
+def test_random_tiny_all_agree():
+    rng = np.random.default_rng(12345)
+    for i in range(2500):
+        n, g = _random_tiny(rng, i)
+        bf, sbf = oracle.brute_force(*g)
+        sw, ssw = oracle.stoer_wagner(*g)
+        noi, snoi, _ = oracle.noi(*g, seed=i)
+        noi_u, _, _ = oracle.noi(*g, capped=False, seed=i + 1)
+        assert bf == sw == noi == noi_u, (i, bf, sw, noi, noi_u)
+        for s in (sbf, ssw, snoi):
+            assert side_ok(s, n)
+            assert oracle.cut_weight(*g, s) == bf
+
+
+def test_noi_medium_seeds_and_cap():
+    # Lemma 1: capping the queue at lambda-hat keeps lambda; the start vertex
+    # (Alg. 3 "insert random vertex") does not change lambda either.
+    for i in range(12):
+        g = graphgen.random_connected(300 + 50 * i, 900 + 100 * i, seed=100 + i, wmax=20)
+        ref = oracle.stoer_wagner(*g)[0]
+        for seed in range(3):
+            lam, side, _ = oracle.noi(*g, capped=bool(seed % 2), seed=seed)
+            assert lam == ref
+            assert oracle.cut_weight(*g, side) == ref
+
+
+def test_planted_small_block_graph():
+    g = graphgen.planted(3, block_n=300, avg_deg=12, cross=3)
+    n = len(g[0]) - 1
+    deg = oracle.degrees(*g)
+    ref, side = oracle.stoer_wagner(*g)
+    assert ref <= min(3, int(deg.min()))
+    lam, s, _ = oracle.noi(*g)
+    assert lam == ref and oracle.cut_weight(*g, s) == ref and side_ok(s, n)
+
+
+def test_degrees_closed_forms():
+    g = graphgen.complete(7, 3)
+    assert (oracle.degrees(*g) == 18).all()
+    g = graphgen.from_edges(3, np.array([0, 0, 1, 2]), np.array([1, 1, 2, 2]),
+                            np.array([2, 3, 4, 50]))
+    assert list(oracle.degrees(*g)) == [5, 9, 4]
+
+
+def _rand_labels(rng, n):
+    nc = int(rng.integers(1, n + 1))
+    lab = rng.integers(0, nc, size=n)
+    lab[rng.permutation(n)[:nc]] = np.arange(nc)  # every block non-empty
+    return lab.astype(np.int32), nc
+
+
+def test_contract_preserves_block_respecting_cuts():
+    rng = np.random.default_rng(7)
+    for i in range(300):
+        n, g = _random_tiny(rng, i)
+        lab, nc = _rand_labels(rng, n)
+        crp, ccol, cw = oracle.contract(*g, lab, nc)
+        # canonical: sorted rows, no self-loops, no zero weights
+        for b in range(nc):
+            row = ccol[crp[b]:crp[b + 1]]
+            assert (np.diff(row) > 0).all() and (row != b).all()
+        assert (cw > 0).all()
+        # total weight: all arcs minus those inside blocks
+        rp, col, w = g
+        src = np.repeat(np.arange(n), np.diff(rp))
+        cross = lab[src] != lab[col]
+        assert cw.sum() == w[cross].astype(np.int64).sum()
+        # every cut of the contracted graph weighs what its preimage weighs
+        for _ in range(4):
+            a = rng.integers(0, 2, size=nc).astype(np.uint8)
+            pre = a[lab]
+            c_sum = 0
+            csrc = np.repeat(np.arange(nc), np.diff(crp))
+            c_sum = int(cw[a[csrc] != a[ccol]].sum()) // 2
+            assert c_sum == oracle.cut_weight(*g, pre)
+
+
+def test_label_prop_cliques_converge_to_min_id():
+    # two disjoint cliques: labels only travel along edges and each clique
+    # settles on one label, the smallest id in it
+    iu, ju = np.triu_indices(6, 1)
+    u = np.concatenate([iu, iu + 6])
+    v = np.concatenate([ju, ju + 6])
+    g = graphgen.from_edges(12, u, v)
+    for seed in range(5):
+        lab = oracle.label_prop(*g, iters=6, seed=seed)
+        assert (lab[:6] == 0).all() and (lab[6:] == 6).all()
+
+
+def test_label_prop_labels_stay_in_component():
+    rng = np.random.default_rng(3)
+    for i in range(50):
+        n, g = _random_tiny(rng, i)
+        lab = oracle.label_prop(*g, iters=3, seed=i)
+        # component of each vertex via brute BFS
+        rp, col, _ = g
+        comp = -np.ones(n, dtype=np.int64)
+        for s in range(n):
+            if comp[s] >= 0:
+                continue
+            stack = [s]
+            comp[s] = s
+            while stack:
+                x = stack.pop()
+                for y in col[rp[x]:rp[x + 1]]:
+                    if comp[y] < 0:
+                        comp[y] = s
+                        stack.append(y)
+        assert (comp[lab] == comp).all()
+        # zero sweeps leave the identity labelling
+        assert (oracle.label_prop(*g, iters=0, seed=i) == np.arange(n)).all()
+
+
+def test_pr_tests_preserve_lambda():
+    # every PR contraction keeps min(lambda-hat, lambda(G / PR)) = lambda(G)
+    rng = np.random.default_rng(11)
+    checked = 0
+    for i in range(600):
+        n, g = _random_tiny(rng, i)
+        if n < 3:
+            continue
+        lam = oracle.brute_force(*g)[0]
+        deg = oracle.degrees(*g)
+        for bound in (int(deg.min()), max(lam, int(deg.min()) - 1), lam):
+            if bound < lam:
+                continue
+            for level in (1, 2, 3, 4):
+                lab = oracle.pr_tests(*g, bound, level)
+                roots, lab2 = np.unique(lab, return_inverse=True)
+                nc = len(roots)
+                if nc == 1:
+                    assert bound == lam
+                    continue
+                crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), nc)
+                lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
+                assert min(bound, lam_c) == lam, (i, level, bound, lam, lam_c)
+                checked += 1
+    assert checked > 1000
+
+
+def test_pr2_strictness_chain():
+    # two K_10 joined by a path x - u1 - u2 - y of unit edges: lambda = 1,
+    # delta = 2.  "2c >= min d" would hold on every path edge and contracting
+    # them all at once would lose the cut of weight 1; the strict test keeps it.
+    a = 10
+    iu, ju = np.triu_indices(a, 1)
+    u = np.concatenate([iu, iu + a, [0, 2 * a, 2 * a + 1]])
+    v = np.concatenate([ju, ju + a, [2 * a, 2 * a + 1, a]])
+    g = graphgen.from_edges(2 * a + 2, u, v)
+    assert oracle.stoer_wagner(*g)[0] == 1
+    lab = oracle.pr_tests(*g, 2, 2)
+    roots, lab2 = np.unique(lab, return_inverse=True)
+    crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+    assert oracle.stoer_wagner(crp.astype(np.int32), ccol, cw.astype(np.int32))[0] == 1
+
+
+def test_pr1_pr4_closed_forms():
+    # PR1: an edge of weight >= bound is always merged.
+    g = graphgen.from_edges(4, np.array([0, 1, 2]), np.array([1, 2, 3]), np.array([5, 1, 5]))
+    lab = oracle.pr_tests(*g, 5, 1)
+    assert lab[0] == lab[1] and lab[2] == lab[3] and lab[1] != lab[2]
+    # PR4 on K_n: c(u,v) + (n - 2) two-hop paths = n - 1 >= bound n - 1.
+    g = graphgen.complete(6)
+    lab = oracle.pr_tests(*g, 5, 4)
+    assert (lab == 0).all()
+    assert len(np.unique(oracle.pr_tests(*g, 5, 3))) == 6  # PR3 needs > d/2
+
+
+def test_planted_4096_two_exact_algorithms_agree():
+    # the small plain-method workload: Stoer-Wagner and NOI agree, lambda <= 8
+    g = graphgen.planted(1)
+    sw, s1 = oracle.stoer_wagner(*g)
+    noi, s2, _ = oracle.noi(*g)
+    assert sw == noi <= 8
+    assert oracle.cut_weight(*g, s1) == sw and oracle.cut_weight(*g, s2) == sw
