@@ -1,0 +1,203 @@
+/*
+ * mc.h -- C ABI of libmincut: exact global minimum cut on one GB300 GPU.
+ *
+ * Method (Henzinger, Noe, Schulz, "Shared-memory Exact Minimum Cuts"):
+ *   Alg. 2 (Parallel Minimum Cut): start from an upper bound lambda-hat
+ *   (minimum weighted degree, Sec. 2.1/3.1.1, optionally lowered by a
+ *   label-propagation clustering bound in the manner of VieCut, Sec. 2.3),
+ *   then repeat
+ *     - Padberg-Rinaldi local tests against lambda-hat (Sec. 2.2, 2.3),
+ *     - many concurrent CAPFOREST scans with priority queues capped at
+ *       lambda-hat (Alg. 1, Sec. 3.1.2 Lemma 1, Sec. 3.2), uniting the ends of
+ *       every edge whose connectivity certificate reaches lambda-hat,
+ *     - a full CAPFOREST scan when nothing was united (Alg. 2, Alg. 3),
+ *     - contraction of the united blocks (Sec. 2.1, Sec. 3.2 "Parallel Graph
+ *       Contraction"), lowering lambda-hat to the minimum degree,
+ *   until one vertex is left.  The smallest cut seen is the minimum cut, and
+ *   its side is kept as in Sec. 3.3.
+ *
+ * All arithmetic on this path is integer and lambda is exact.
+ *
+ * Graphs are undirected, given as a symmetric CSR with int32 offsets,
+ * neighbours and non-negative int32 weights: every edge {u, v} of weight c
+ * appears as arc (u -> v, c) in row u and as arc (v -> u, c) in row v.
+ * Self-loops and zero weights are dropped, parallel arcs are summed
+ * (Sec. 2.1 merges parallel edges the same way).
+ *
+ * Errors: every call returns MC_OK (0) or a negative MC_E* code; nothing
+ * throws across this boundary.  mc_strerror() gives a message, including
+ * the CUDA error string for MC_ECUDA.
+ *
+ * Threads and streams: calls on one mc_graph must not overlap; different
+ * graphs may be used from different threads on different streams.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define MC_OK 0
+#define MC_EINVAL (-1)     /* malformed input or arguments (see each call)   */
+#define MC_ENOMEM (-2)     /* device or host allocation failed               */
+#define MC_ECUDA (-3)      /* a CUDA call failed; mc_strerror has the detail */
+#define MC_ETIMEOUT (-4)   /* a bounded device wait gave up                  */
+#define MC_EOVERFLOW (-5)  /* a weighted degree or bound does not fit        */
+#define MC_EINTERNAL (-6)  /* an internal invariant failed (a bug)           */
+
+/* ---- flags for mc_graph_create ----------------------------------------- */
+#define MC_DEVICE_PTRS 1   /* row_ptr/col/w are device pointers              */
+#define MC_TRUST_INPUT 2   /* skip the symmetry check (still canonicalised)  */
+
+/* ---- options ------------------------------------------------------------ */
+#define MC_PQ_LIFO 0       /* BStack order inside a bucket (Sec. 3.1.3)       */
+#define MC_PQ_FIFO 1       /* BQueue order inside a bucket (Sec. 3.1.3)       */
+
+#define MC_BOUND_DEGREE 0  /* lambda-hat = minimum weighted degree            */
+#define MC_BOUND_LP 1      /* + label-propagation clustering bound (VieCut)   */
+
+typedef struct mc_options {
+    int32_t pq_order;        /* MC_PQ_LIFO (default) or MC_PQ_FIFO             */
+    int32_t bound;           /* MC_BOUND_DEGREE (default) or MC_BOUND_LP       */
+    int32_t pr_level;        /* Padberg-Rinaldi tests 1..pr_level, 0 = off;
+                                default 2                                       */
+    int32_t scans_per_round; /* concurrent CAPFOREST warps, 0 = auto           */
+    int32_t region_budget;   /* max vertices touched by one scan, 0 = auto     */
+    int32_t lp_iters;        /* label-propagation sweeps for MC_BOUND_LP, 0=auto*/
+    uint64_t seed;           /* start vertices / LP parity                      */
+    void *cuda_stream;       /* cudaStream_t to run on; NULL = the graph's own */
+} mc_options;
+
+/* Per-call statistics (all optional). */
+typedef struct mc_stats {
+    int32_t rounds;          /* contraction rounds of Alg. 2                    */
+    int32_t fallback_rounds; /* rounds that needed the full CAPFOREST scan      */
+    int64_t bound_initial;   /* lambda-hat before the first round               */
+    int64_t n_input;         /* vertices of the canonical input                 */
+    int64_t m_input;         /* undirected edges of the canonical input         */
+    double ms_total;         /* device time of the whole call                   */
+    double ms_bound;         /* initial bound (degrees / LP)                    */
+    double ms_pr;            /* Padberg-Rinaldi tests                           */
+    double ms_capforest;     /* CAPFOREST scans (parallel + fallback)           */
+    double ms_contract;      /* union-find flatten, relabel, sort, rebuild      */
+    int64_t bytes_alg;       /* algorithmic bytes the method had to move        */
+    int64_t scanned_arcs;    /* arcs read by CAPFOREST scans                    */
+    int64_t scanned_verts;   /* vertices scanned by CAPFOREST scans             */
+    int64_t kernel_launches; /* CUDA kernels launched by the call               */
+    int32_t scan_launches;   /* launches of the concurrent-scan kernel          */
+    int32_t pad_;
+    double ms_scan_kernel;   /* device time of those launches (events)          */
+} mc_stats;
+
+typedef struct mc_graph mc_graph; /* opaque; owns its device copies */
+
+/* Fill *opt with the defaults (always succeeds for a non-NULL opt). */
+int mc_options_default(mc_options *opt);
+
+/*
+ * mc_graph_create -- copy and canonicalise a graph on the current device.
+ *   n        vertices, >= 2 (a cut needs two non-empty sides, Sec. 2.1)
+ *   row_ptr  n+1 int32 offsets, row_ptr[0] = 0, non-decreasing
+ *   col      row_ptr[n] int32 neighbours in [0, n)
+ *   w        row_ptr[n] int32 weights >= 0
+ *   flags    MC_DEVICE_PTRS: the arrays live on the device (read on the
+ *            graph's stream); otherwise host memory.  MC_TRUST_INPUT: skip
+ *            the symmetry check.
+ *   out      receives the new graph; the caller keeps ownership of its arrays
+ *            (they are copied) and must call mc_graph_destroy().
+ * Errors: MC_EINVAL for n < 2, a bad row_ptr, a neighbour out of range, a
+ * negative weight, or (unless trusted) an arc (u,v,c) without its mirror
+ * (v,u,c) after merging parallel arcs; MC_EOVERFLOW if a weighted degree
+ * reaches 2^62; MC_ENOMEM; MC_ECUDA.
+ */
+int mc_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                    const int32_t *w, int32_t flags, mc_graph **out);
+
+int mc_graph_destroy(mc_graph *g);
+
+/* Vertices and undirected edges of the canonical graph. */
+int mc_graph_size(const mc_graph *g, int64_t *n, int64_t *m);
+
+/*
+ * mc_min_cut -- lambda(G) and one side of a minimum cut (Alg. 2, Sec. 3.3).
+ *   opt          NULL for defaults
+ *   lambda_out   host int64: the exact minimum cut value
+ *   side_bitmap  NULL, or ceil(n/32) uint32 words (host memory, or device
+ *                memory if the graph was created with MC_DEVICE_PTRS):
+ *                bit v (word v/32, bit v%32) = 1 iff vertex v is on the side
+ *                that does not contain vertex 0; unused high bits are 0
+ *   stats        NULL or filled
+ * A disconnected graph has lambda = 0 and the side is every component but
+ * vertex 0's.  The call is synchronous: it returns after the device work.
+ * Errors: MC_EINVAL (NULL g/lambda_out), MC_EOVERFLOW (minimum weighted
+ * degree >= 2^31 - 1, which the int32 scan arithmetic cannot hold),
+ * MC_ECUDA, MC_ETIMEOUT, MC_EINTERNAL.
+ */
+int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,
+               uint32_t *side_bitmap, mc_stats *stats);
+
+/*
+ * mc_batch_min_cut -- lambda for each of G independent graphs.
+ *   vtx_off   G+1 int64 vertex offsets (graph g has vtx_off[g+1]-vtx_off[g]
+ *             vertices, each >= 2)
+ *   arc_off   G+1 int64 arc offsets
+ *   row_ptr   concatenated per-graph LOCAL offsets: graph g's n_g+1 entries
+ *             start at row_ptr[vtx_off[g] + g] and count from 0
+ *   col, w    concatenated per-graph arcs with LOCAL neighbour ids
+ *   lambdas   G int64 results (host)
+ *   bitmaps   NULL, or per-graph side bitmaps: graph g's ceil(n_g/32) words
+ *             start at bitmap_word_off[g] (host)
+ *   bitmap_word_off  G+1 int64, required when bitmaps is non-NULL
+ * Every graph must be connected or not, weights >= 0, symmetric.
+ * Errors as mc_graph_create / mc_min_cut, for the first failing graph.
+ */
+int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
+                     const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                     const mc_options *opt, int64_t *lambdas, uint32_t *bitmaps,
+                     const int64_t *bitmap_word_off, mc_stats *stats);
+
+/* Message for an error code (thread-local detail for MC_ECUDA). */
+const char *mc_strerror(int code);
+
+/* ---- step-level entry points (same kernels as mc_min_cut) ---------------
+ * These expose single steps of the path on a created graph for parity
+ * testing.  All arrays are host memory, sized as stated.                  */
+
+/* Canonical CSR of the graph: row_ptr n+1, col/w m2 = 2*m entries, rows
+ * sorted by neighbour.  Pass NULL arrays to query nothing but sizes.      */
+int mc_graph_export(const mc_graph *g, int32_t *row_ptr, int32_t *col, int32_t *w);
+
+/* Weighted degrees (Sec. 2.1), n int64. */
+int mc_step_degrees(mc_graph *g, int64_t *deg);
+
+/* Contract the graph by block labels lab[v] in [0, nc) (Sec. 2.1, every
+ * block at once): writes the canonical contracted CSR (row_ptr nc+1,
+ * col/w up to 2*m entries, weights clamped to `clamp` if clamp > 0) and
+ * its arc count to *arcs_out.                                             */
+int mc_step_contract(mc_graph *g, const int32_t *lab, int32_t nc, int64_t clamp,
+                     int32_t *row_ptr, int32_t *col, int32_t *w, int64_t *arcs_out);
+
+/* Padberg-Rinaldi tests 1..level against bound `lam` (reading stated in
+ * DESIGN and in the kernel source); labels[v] = smallest vertex of v's
+ * block in the graph of passing edges.                                    */
+int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels);
+
+/* One round of concurrent capped CAPFOREST scans (Alg. 1) at bound `lam`:
+ * labels[v] = smallest vertex of v's union-find block, *lam_out = the bound
+ * after the scans' alpha updates, *unions_out = successful unions.         */
+int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt,
+                      int32_t *labels, int64_t *lam_out, int64_t *unions_out);
+
+/* `iters` label-propagation sweeps (reading stated in DESIGN and in the
+ * kernel source); labels n int32.                                         */
+int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *labels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

@@ -1,0 +1,474 @@
+// mc_api.cu -- the C ABI (include/mc.h) and the host driver of Alg. 2.
+//
+// Driver per round on the current graph G_C (Alg. 2, Sec. 3.3):
+//   union-find reset -> Padberg-Rinaldi tests -> concurrent capped CAPFOREST
+//   (Alg. 1) -> if nothing was united: one full CAPFOREST scan (Alg. 3) ->
+//   contraction (Sec. 3.2) -> lambda-hat = min(lambda-hat, delta(G_C)).
+// Every improvement of lambda-hat snapshots its side as a bitmap over the
+// original vertices (Sec. 3.3): a scan's prefix for an alpha cut, the
+// preimage of a contracted vertex for a degree cut.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mc_internal.cuh"
+
+using namespace mc;
+
+struct mc_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n0 = 0;
+    i64 arcs0 = 0;
+    DevGraph G0, Ga, Gb;
+    Work w;
+    int ncomp = 1;
+    i64 delta0 = 0;
+    int argmin0 = 0;
+    bool device_ptrs = false;
+};
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t s_) : s(s_) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    double ms() {
+        float t = 0;
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&t, a, b);
+        cudaEventRecord(a, s);
+        return t;
+    }
+};
+
+int read_i32(const int *p, bool dev, int *out, cudaStream_t s) {
+    if (!dev) {
+        *out = *p;
+        return MC_OK;
+    }
+    MC_CUDA(cudaMemcpyAsync(out, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+void destroy_all(mc_graph *g) {
+    if (!g) return;
+    cudaStream_t s = g->stream;
+    if (s) cudaStreamSynchronize(s);
+    graph_free(g->G0, s);
+    graph_free(g->Ga, s);
+    graph_free(g->Gb, s);
+    work_free(g->w, s);
+    if (s) cudaStreamDestroy(s);
+    delete g;
+}
+
+cudaStream_t pick_stream(mc_graph *g, const mc_options *o) {
+    return (o && o->cuda_stream) ? static_cast<cudaStream_t>(o->cuda_stream) : g->stream;
+}
+
+int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                int32_t flags, mc_graph **out) {
+    if (!out || !row_ptr || n < 2) return MC_EINVAL;
+    *out = nullptr;
+    const bool dev = (flags & MC_DEVICE_PTRS) != 0;
+    mc_graph *g = new mc_graph();
+    g->device_ptrs = dev;
+    cudaGetDevice(&g->device);
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaStreamCreate");
+            delete g;
+            return MC_ECUDA;
+        }
+    }
+    cudaStream_t s = g->stream;
+    int arcs_raw = 0;
+    int rc = read_i32(row_ptr + n, dev, &arcs_raw, s);
+    if (rc == MC_OK && arcs_raw < 0) rc = MC_EINVAL;
+    if (rc == MC_OK && arcs_raw > 0 && (!col || !w)) rc = MC_EINVAL;
+    if (rc != MC_OK) {
+        destroy_all(g);
+        return rc;
+    }
+    const i64 A = arcs_raw > 0 ? arcs_raw : 1;
+    g->n0 = n;
+    if ((rc = work_alloc(g->w, n, A, s)) != MC_OK || (rc = graph_alloc(g->G0, n, A, s)) != MC_OK ||
+        (rc = graph_alloc(g->Ga, n, A, s)) != MC_OK || (rc = graph_alloc(g->Gb, n, A, s)) != MC_OK) {
+        destroy_all(g);
+        return rc;
+    }
+    const int *drp = row_ptr, *dcol = col, *dw = w;
+    if (!dev) {
+        // stage the raw arrays in Ga (rp, src) and Gb (src)
+        cudaError_t e = cudaMemcpyAsync(g->Ga.rp, row_ptr, sizeof(int) * ((size_t)n + 1),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && arcs_raw > 0)
+            e = cudaMemcpyAsync(g->Ga.src, col, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && arcs_raw > 0)
+            e = cudaMemcpyAsync(g->Gb.src, w, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaMemcpyAsync(input)");
+            destroy_all(g);
+            return MC_ECUDA;
+        }
+        drp = g->Ga.rp;
+        dcol = g->Ga.src;
+        dw = g->Gb.src;
+    }
+    rc = canonicalize(n, drp, dcol, dw, (flags & MC_TRUST_INPUT) == 0, g->G0, g->w, s);
+    if (rc == MC_OK) rc = min_degree(g->G0, g->w, s);
+    if (rc == MC_OK) rc = status_read(g->w, s);
+    if (rc == MC_OK) {
+        g->delta0 = g->w.h_st->mindeg;
+        g->argmin0 = g->w.h_st->argmin;
+        if (g->delta0 >= (1LL << 62)) rc = MC_EOVERFLOW;
+    }
+    if (rc == MC_OK) rc = connected_components(g->G0, g->w, &g->ncomp, s);
+    if (rc != MC_OK) {
+        destroy_all(g);
+        return rc;
+    }
+    g->arcs0 = g->G0.arcs;
+    *out = g;
+    return MC_OK;
+}
+
+struct SolveOut {
+    i64 lam = 0;
+    mc_stats st{};
+};
+
+// Alg. 2 on g; leaves the side bitmap in g->w.best_side (canonical polarity)
+int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) {
+    Work &w = g->w;
+    const int n0 = g->n0;
+    mc_stats &S = out.st;
+    memset(&S, 0, sizeof(S));
+    S.n_input = n0;
+    S.m_input = g->arcs0 / 2;
+    Timer total(s), ph(s);
+    i64 bytes = 0;
+    const long long launches0 = g_launches;
+    cudaEvent_t ka, kb;
+    cudaEventCreate(&ka);
+    cudaEventCreate(&kb);
+    struct EvFree {
+        cudaEvent_t a, b;
+        ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev_free{ka, kb};
+
+    if (g->ncomp > 1) {
+        int nc = 0;
+        MC_TRY(connected_components(g->G0, w, &nc, s));
+        MC_TRY(side_from_component(w, n0, s));
+        MC_TRY(side_canon(w, n0, s));
+        out.lam = 0;
+        S.ms_total = total.ms();
+        return MC_OK;
+    }
+    if (g->delta0 >= (i64)0x7FFFFFFE - 1) return MC_EOVERFLOW;
+
+    // lambda-hat = delta with the trivial cut of a minimum-degree vertex
+    MC_TRY(iota_i32(w.orig, n0, s));
+    i64 lam = g->delta0;
+    MC_TRY(side_from_vertex(w, n0, g->argmin0, s));
+    S.bound_initial = lam;
+    bytes += g->G0.arcs * 8 + (i64)n0 * 12;  // degree sweep
+    S.ms_bound = ph.ms();
+
+    DevGraph cur = g->G0;
+    DevGraph *nxt = &g->Ga;
+    ScanConfig cfg;
+    cfg.pq_fifo = o.pq_order == MC_PQ_FIFO;
+    cfg.warps = o.scans_per_round;
+    cfg.budget = o.region_budget;
+    cfg.seed = o.seed;
+    int rounds = 0, fallbacks = 0, guard = 0;
+    while (cur.n >= 2 && lam > 0) {
+        if (++guard > 4 * n0 + 64) return MC_EINTERNAL;
+        cfg.round = rounds + guard;
+        MC_TRY(union_find_init(w.par, cur.n, s));
+        MC_TRY(round_reset(w, lam, s));
+        if (o.pr_level > 0) {
+            MC_TRY(pr_tests(cur, w, lam, o.pr_level, s));
+            bytes += cur.arcs * 16;
+        }
+        S.ms_pr += ph.ms();
+        MC_CUDA(cudaEventRecord(ka, s));
+        MC_TRY(capforest_parallel(cur, w, cfg, s));
+        MC_CUDA(cudaEventRecord(kb, s));
+        MC_TRY(status_read(w, s));
+        {
+            float t = 0;
+            cudaEventElapsedTime(&t, ka, kb);
+            S.ms_scan_kernel += t;
+            S.scan_launches += 1;
+        }
+        Status st = *w.h_st;
+        S.scanned_arcs += st.scanned_arcs;
+        S.scanned_verts += st.scanned_verts;
+        bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
+        if (st.lam < lam && st.best_scan > 0) {
+            MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
+            lam = st.lam;
+        }
+        i64 unions = st.unions;
+        if (unions == 0) {
+            const i64 lam_before = lam;
+            MC_TRY(capforest_full(cur, w, cfg, s));
+            MC_TRY(status_read(w, s));
+            st = *w.h_st;
+            S.scanned_arcs += st.scanned_arcs;
+            S.scanned_verts += st.scanned_verts;
+            bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
+            if (st.lam < lam && st.best_scan > 0) {
+                MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
+                lam = st.lam;
+            }
+            unions = st.unions;
+            ++fallbacks;
+            if (unions == 0) {
+                S.ms_capforest += ph.ms();
+                if (lam < lam_before) continue;  // lambda-hat dropped inside the scan: rescan
+                set_error_detail("full CAPFOREST scan marked no edge");
+                return MC_EINTERNAL;
+            }
+        }
+        S.ms_capforest += ph.ms();
+        MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s));
+        MC_TRY(orig_update(w, n0, s));
+        MC_TRY(min_degree(*nxt, w, s));
+        MC_TRY(status_read(w, s));
+        if (w.h_st->err & kErrOverflow) return MC_EOVERFLOW;
+        bytes += cur.arcs * 20 + w.h_st->count * 12 + (i64)cur.n * 16 + (i64)n0 * 8;
+        if (nxt->n >= 2 && w.h_st->mindeg < lam) {
+            lam = w.h_st->mindeg;
+            MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
+        }
+        S.ms_contract += ph.ms();
+        cur = *nxt;
+        nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
+        ++rounds;
+    }
+    MC_TRY(side_canon(w, n0, s));
+    S.rounds = rounds;
+    S.fallback_rounds = fallbacks;
+    S.bytes_alg = bytes;
+    S.kernel_launches = g_launches - launches0;
+    out.lam = lam;
+    S.ms_total = total.ms();
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_options_default(mc_options *opt) {
+    if (!opt) return MC_EINVAL;
+    memset(opt, 0, sizeof(*opt));
+    opt->pq_order = MC_PQ_LIFO;
+    opt->bound = MC_BOUND_DEGREE;
+    opt->pr_level = 2;
+    opt->scans_per_round = 0;
+    opt->region_budget = 0;
+    opt->lp_iters = 0;
+    opt->seed = 0x1234ABCDULL;
+    opt->cuda_stream = nullptr;
+    return MC_OK;
+}
+
+int mc_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                    int32_t flags, mc_graph **out) {
+    return create_impl(n, row_ptr, col, w, flags, out);
+}
+
+int mc_graph_destroy(mc_graph *g) {
+    if (!g) return MC_EINVAL;
+    destroy_all(g);
+    return MC_OK;
+}
+
+int mc_graph_size(const mc_graph *g, int64_t *n, int64_t *m) {
+    if (!g) return MC_EINVAL;
+    if (n) *n = g->n0;
+    if (m) *m = g->arcs0 / 2;
+    return MC_OK;
+}
+
+int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out, uint32_t *side_bitmap,
+               mc_stats *stats) {
+    if (!g || !lambda_out) return MC_EINVAL;
+    mc_options o;
+    if (opt) o = *opt; else mc_options_default(&o);
+    if (o.pr_level < 0 || o.pr_level > 4) return MC_EINVAL;
+    cudaStream_t s = pick_stream(g, opt);
+    SolveOut so;
+    int rc = solve_impl(g, o, s, so);
+    if (rc != MC_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    *lambda_out = so.lam;
+    if (side_bitmap) {
+        size_t bytes = sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32);
+        MC_CUDA(cudaMemcpyAsync(side_bitmap, g->w.best_side, bytes,
+                                g->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (stats) *stats = so.st;
+    return MC_OK;
+}
+
+int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off, const int32_t *row_ptr,
+                     const int32_t *col, const int32_t *w, const mc_options *opt, int64_t *lambdas,
+                     uint32_t *bitmaps, const int64_t *bitmap_word_off, mc_stats *stats) {
+    if (G < 0 || !vtx_off || !arc_off || !row_ptr || !lambdas) return MC_EINVAL;
+    if (bitmaps && !bitmap_word_off) return MC_EINVAL;
+    mc_stats agg;
+    memset(&agg, 0, sizeof(agg));
+    for (int32_t k = 0; k < G; ++k) {
+        const int64_t n = vtx_off[k + 1] - vtx_off[k];
+        if (n < 2 || n > 0x7FFFFFFF) return MC_EINVAL;
+        const int32_t *rp = row_ptr + vtx_off[k] + k;
+        const int64_t a0 = arc_off[k];
+        if (rp[n] != (int32_t)(arc_off[k + 1] - a0)) return MC_EINVAL;
+        mc_graph *g = nullptr;
+        int rc = mc_graph_create((int32_t)n, rp, col + a0, w + a0, 0, &g);
+        if (rc != MC_OK) return rc;
+        mc_stats st;
+        rc = mc_min_cut(g, opt, &lambdas[k], bitmaps ? bitmaps + bitmap_word_off[k] : nullptr, &st);
+        mc_graph_destroy(g);
+        if (rc != MC_OK) return rc;
+        agg.rounds += st.rounds;
+        agg.fallback_rounds += st.fallback_rounds;
+        agg.n_input += st.n_input;
+        agg.m_input += st.m_input;
+        agg.ms_total += st.ms_total;
+        agg.bytes_alg += st.bytes_alg;
+        agg.scanned_arcs += st.scanned_arcs;
+    }
+    if (stats) *stats = agg;
+    return MC_OK;
+}
+
+const char *mc_strerror(int code) {
+    static thread_local std::string msg;
+    switch (code) {
+        case MC_OK: return "ok";
+        case MC_EINVAL: return "invalid argument or malformed graph";
+        case MC_ENOMEM: return "out of memory";
+        case MC_ECUDA: msg = "CUDA error: " + error_detail(); return msg.c_str();
+        case MC_ETIMEOUT: return "a bounded device wait timed out";
+        case MC_EOVERFLOW: return "weight, degree or bound overflow";
+        case MC_EINTERNAL: msg = "internal error: " + error_detail(); return msg.c_str();
+        default: return "unknown error";
+    }
+}
+
+int mc_graph_export(const mc_graph *g, int32_t *row_ptr, int32_t *col, int32_t *w) {
+    if (!g) return MC_EINVAL;
+    cudaStream_t s = g->stream;
+    if (row_ptr)
+        MC_CUDA(cudaMemcpyAsync(row_ptr, g->G0.rp, sizeof(int) * ((size_t)g->n0 + 1), cudaMemcpyDeviceToHost, s));
+    if ((col || w) && g->arcs0 > 0) {
+        std::vector<int2> adj((size_t)g->arcs0);
+        MC_CUDA(cudaMemcpyAsync(adj.data(), g->G0.adj, sizeof(int2) * (size_t)g->arcs0, cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        for (i64 i = 0; i < g->arcs0; ++i) {
+            if (col) col[i] = adj[(size_t)i].x;
+            if (w) w[i] = adj[(size_t)i].y;
+        }
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+int mc_step_degrees(mc_graph *g, int64_t *deg) {
+    if (!g || !deg) return MC_EINVAL;
+    MC_CUDA(cudaMemcpyAsync(deg, g->G0.deg, sizeof(i64) * (size_t)g->n0, cudaMemcpyDeviceToHost, g->stream));
+    MC_CUDA(cudaStreamSynchronize(g->stream));
+    return MC_OK;
+}
+
+int mc_step_contract(mc_graph *g, const int32_t *lab, int32_t nc, int64_t clamp, int32_t *row_ptr,
+                     int32_t *col, int32_t *w, int64_t *arcs_out) {
+    if (!g || !lab || nc < 1 || nc > g->n0 || !row_ptr || !arcs_out) return MC_EINVAL;
+    for (int v = 0; v < g->n0; ++v)
+        if (lab[v] < 0 || lab[v] >= nc) return MC_EINVAL;
+    cudaStream_t s = g->stream;
+    MC_CUDA(cudaMemcpyAsync(g->w.lab, lab, sizeof(int) * (size_t)g->n0, cudaMemcpyHostToDevice, s));
+    MC_TRY(round_reset(g->w, 0, s));
+    MC_TRY(contract_graph(g->G0, g->Ga, g->w, clamp > 0 ? clamp : LLONG_MAX, false, nc, s));
+    MC_TRY(status_read(g->w, s));
+    if (g->w.h_st->err & kErrOverflow) return MC_EOVERFLOW;
+    *arcs_out = g->Ga.arcs;
+    MC_CUDA(cudaMemcpyAsync(row_ptr, g->Ga.rp, sizeof(int) * ((size_t)nc + 1), cudaMemcpyDeviceToHost, s));
+    if (g->Ga.arcs > 0 && (col || w)) {
+        std::vector<int2> adj((size_t)g->Ga.arcs);
+        MC_CUDA(cudaMemcpyAsync(adj.data(), g->Ga.adj, sizeof(int2) * (size_t)g->Ga.arcs, cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        for (i64 i = 0; i < g->Ga.arcs; ++i) {
+            if (col) col[i] = adj[(size_t)i].x;
+            if (w) w[i] = adj[(size_t)i].y;
+        }
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels) {
+    if (!g || !labels || level < 0 || level > 4) return MC_EINVAL;
+    cudaStream_t s = g->stream;
+    MC_TRY(union_find_init(g->w.par, g->n0, s));
+    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(pr_tests_budget(g->G0, g->w, lam, level, -1, s));
+    MC_TRY(flatten_labels(g->w, g->n0, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *labels, int64_t *lam_out,
+                      int64_t *unions_out) {
+    if (!g || !labels) return MC_EINVAL;
+    mc_options o;
+    if (opt) o = *opt; else mc_options_default(&o);
+    cudaStream_t s = g->stream;
+    ScanConfig cfg;
+    cfg.pq_fifo = o.pq_order == MC_PQ_FIFO;
+    cfg.warps = o.scans_per_round;
+    cfg.budget = o.region_budget;
+    cfg.seed = o.seed;
+    MC_TRY(union_find_init(g->w.par, g->n0, s));
+    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));
+    MC_TRY(flatten_labels(g->w, g->n0, s));
+    MC_TRY(status_read(g->w, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (lam_out) *lam_out = g->w.h_st->lam;
+    if (unions_out) *unions_out = g->w.h_st->unions;
+    return MC_OK;
+}
+
+int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *labels) {
+    if (!g || !labels || iters < 0) return MC_EINVAL;
+    (void)seed;
+    return MC_EINVAL;
+}
+
+}  // extern "C"

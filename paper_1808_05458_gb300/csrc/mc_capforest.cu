@@ -1,0 +1,581 @@
+// mc_capforest.cu -- concurrent capped CAPFOREST scans (Alg. 1) and the
+// full single scan fallback (Alg. 3).
+//
+// One warp runs one scan.  Thousands of warps scan at once from seeded start
+// vertices; a vertex is scanned by the first scan that claims it in the
+// shared owner array T (atomicCAS, the paper's shared visited array with
+// "every vertex is visited only once", Sec. 3.2).  A scan that pops a vertex
+// owned by another scan blacklists it and moves on without touching it
+// (Alg. 1, Lemma 2 part 3).
+//
+// Per scan, in the warp's shared memory:
+//   * a hash table vertex -> r(v) (exact int32 connection weight to the
+//     scanned set, saturating) for every vertex the scan touched; the
+//     entry holds DONE once the vertex is scanned or blacklisted;
+//   * a bucket priority queue over keys min(r, C), C = lambda-hat when the
+//     scan starts (Lemma 1, Sec. 3.1.2), with a bitmap of non-empty buckets;
+//     bucket lists are LIFO (BStack) or FIFO (BQueue) (Sec. 3.1.3).  Entries
+//     are lazy: raising a key pushes a new entry; stale ones are dropped at
+//     pop time.  With more keys than buckets the buckets are ranges and a
+//     pop walks its bucket for the largest key, so the order stays exact.
+// Each arc scan of (x, y, c) with y neither scanned nor blacklisted here:
+//   if r(y) < lambda-hat <= r(y) + c: union(x, y)       (Alg. 1)
+//   r(y) += c; key(y) = min(r(y), C)  (never lowered)
+// Each scanned x updates alpha += c(x) - 2 r(x) = c(S), the cut between the
+// scanned set S and the rest, and lowers lambda-hat while S != V (Alg. 1).
+// A scan ends when its queue is empty or its table reaches its budget; early
+// termination keeps every union valid (Lemma 2 part 2).  If a table cannot
+// take a neighbour, that arc is left unscanned -- Lemma 1's argument with the
+// arc's weight lowered to 0 -- and the scan stops reporting alpha.
+#include <cstdio>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+constexpr int kDone = -1;
+constexpr int kSat = 0x7FFFFFFE;  // saturation value of r
+
+__device__ __forceinline__ int sat_add(int r, int c) { return r > kSat - c ? kSat : r + c; }
+
+// ------------------------------------------------------- bucket queue ----
+template <class Idx, int NB>
+struct BucketQ {
+    int *head;
+    int *tail;
+    u32 *bits;
+    Idx *eslot;
+    Idx *enext;
+    int *top;
+    int cap;   // pool entries
+    int C;     // key cap
+    bool coarse;
+    bool fifo;
+    static constexpr Idx NIL = (Idx)(-1);
+
+    __device__ __forceinline__ int bucket(int k) const {
+        return coarse ? (int)(((long long)k * NB) / ((long long)C + 1)) : k;
+    }
+    __device__ __forceinline__ int nxt(int e) const {
+        Idx v = enext[e];
+        return v == NIL ? -1 : (int)v;
+    }
+};
+
+// lanes with `want` push (slot s, key k); all lanes call.  false = no room
+template <class Idx, int NB>
+__device__ bool pq_push(BucketQ<Idx, NB> &q, bool want, int s, int k) {
+    const int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return true;
+    int base = 0;
+    if (lane == 0) {
+        base = *q.top;
+        if (base + __popc(m) > q.cap) base = -1;
+        else *q.top = base + __popc(m);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base < 0) return false;
+    int e = base + __popc(m & ((1u << lane) - 1u));
+    int b = want ? q.bucket(k) : 0;
+    if (want) {
+        q.eslot[e] = (Idx)s;
+        q.enext[e] = q.NIL;
+    }
+    __syncwarp();
+    if (want) {
+        if (!q.fifo) {
+            int old = atomicExch(&q.head[b], e);
+            q.enext[e] = (Idx)old;
+        } else {
+            int old = atomicExch(&q.tail[b], e);
+            if (old < 0) q.head[b] = e;
+            else q.enext[old] = (Idx)e;
+        }
+        atomicOr(&q.bits[b >> 5], 1u << (b & 31));
+    }
+    __syncwarp();
+    return true;
+}
+
+// warp-cooperative pop of a maximum key; returns the slot or -1 if empty.
+// rv[slot] is the slot's r value or kDone.
+template <class Idx, int NB>
+__device__ int pq_pop(BucketQ<Idx, NB> &q, const int *rv) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        u32 word = lane < NB / 32 ? q.bits[lane] : 0u;
+        unsigned m = __ballot_sync(0xffffffffu, word != 0u);
+        if (!m) return -1;
+        int wl = 31 - __clz(m);
+        u32 wv = __shfl_sync(0xffffffffu, word, wl);
+        int b = wl * 32 + 31 - __clz(wv);
+        int found = -1;
+        if (lane == 0) {
+            int prev = -1, e = q.head[b];
+            int best = -1, bestprev = -1, bestkey = -1;
+            while (e >= 0) {
+                int s = (int)q.eslot[e];
+                int nx = q.nxt(e);
+                int r = rv[s];
+                int key = r < q.C ? r : q.C;
+                bool valid = r != kDone && q.bucket(key) == b;
+                if (!valid) {
+                    if (prev < 0) q.head[b] = nx; else q.enext[prev] = nx < 0 ? q.NIL : (Idx)nx;
+                    if (q.fifo && nx < 0) q.tail[b] = prev;
+                    e = nx;
+                    continue;
+                }
+                if (key > bestkey) { bestkey = key; best = e; bestprev = prev; }
+                if (!q.coarse || key == q.C) break;
+                prev = e;
+                e = nx;
+            }
+            if (best >= 0) {
+                int nx = q.nxt(best);
+                if (bestprev < 0) q.head[b] = nx; else q.enext[bestprev] = nx < 0 ? q.NIL : (Idx)nx;
+                if (q.fifo && nx < 0) q.tail[b] = bestprev;
+                found = (int)q.eslot[best];
+            }
+            if (q.head[b] < 0) {
+                q.bits[b >> 5] &= ~(1u << (b & 31));
+                q.tail[b] = -1;
+            }
+        }
+        found = __shfl_sync(0xffffffffu, found, 0);
+        __syncwarp();
+        if (found >= 0) return found;
+    }
+}
+
+// ------------------------------------------------------------- tables ----
+// shared-memory hash table of one warp's scan
+template <int HC, int NB>
+struct ScanSmem {
+    int key[HC];
+    int val[HC];
+    unsigned short eslot[2 * HC];
+    unsigned short enext[2 * HC];
+    int head[NB];
+    int tail[NB];
+    u32 bits[NB / 32];
+    int top;
+    int used;
+};
+
+template <int HC>
+struct LogHC;
+template <> struct LogHC<512> { static constexpr int v = 9; };
+template <> struct LogHC<1024> { static constexpr int v = 10; };
+template <> struct LogHC<2048> { static constexpr int v = 11; };
+
+template <int HC, int NB>
+struct HashTable {
+    ScanSmem<HC, NB> *sm;
+    int limit;
+    __device__ __forceinline__ int *val() const { return sm->val; }
+    // slot of y, inserting it; -1 if the table refuses a new vertex
+    __device__ __forceinline__ int find(int y) const {
+        volatile int *key = sm->key;
+        unsigned h = ((unsigned)y * 2654435761u) >> (32 - LogHC<HC>::v);
+        for (int p = 0; p < HC; ++p) {
+            int k = key[h];
+            if (k == y) return (int)h;
+            if (k == -1) {
+                if (*(volatile int *)&sm->used >= limit) return -1;
+                int old = atomicCAS(&sm->key[h], -1, y);
+                if (old == -1) {
+                    atomicAdd(&sm->used, 1);
+                    sm->val[h] = 0;
+                    return (int)h;
+                }
+                if (old == y) return (int)h;
+            }
+            h = (h + 1) & (HC - 1);
+        }
+        return -1;
+    }
+    __device__ __forceinline__ int vertex(int slot) const { return sm->key[slot]; }
+};
+
+// dense table of the full scan: slot = vertex, r in global memory
+struct DenseTable {
+    int *r;
+    __device__ __forceinline__ int *val() const { return r; }
+    __device__ __forceinline__ int find(int y) const { return y; }
+    __device__ __forceinline__ int vertex(int slot) const { return slot; }
+};
+
+struct ScanArgs {
+    DevGraph g;
+    int *par, *T, *order;
+    Status *st;
+    i64 *rec_alpha;
+    int *rec_len;
+    u64 perm_a, perm_b;
+    int limit;
+};
+
+struct Counters {
+    long long arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
+};
+
+// garbage-collect a hash table's queue: rebuild every bucket list from the
+// live (touched, not DONE) slots
+template <int HC, int NB>
+__device__ void pq_rebuild(BucketQ<unsigned short, NB> &q, ScanSmem<HC, NB> &sm) {
+    const int lane = threadIdx.x & 31;
+    for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
+    if (lane < NB / 32) sm.bits[lane] = 0;
+    if (lane == 0) sm.top = 0;
+    __syncwarp();
+    for (int i0 = 0; i0 < HC; i0 += 32) {
+        int i = i0 + lane;
+        int r = sm.val[i];
+        bool live = sm.key[i] != -1 && r != kDone;
+        pq_push(q, live, i, r < q.C ? r : q.C);
+    }
+}
+
+// One scan of Alg. 1 from `start` with id `sid` and key cap C.
+template <class Table, class Q, bool HASHED>
+__device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt,
+                         void *smem_for_gc) {
+    const int lane = threadIdx.x & 31;
+    const int n = A.g.n;
+    const int C = q.C;
+    int *rv = tab.val();
+    {
+        int s = lane == 0 ? tab.find(start) : 0;
+        s = __shfl_sync(0xffffffffu, s, 0);
+        pq_push(q, lane == 0, s, 0);
+    }
+    long long alpha = 0, best = LLONG_MAX;
+    int nS = 0, best_len = 0;
+    bool alpha_ok = true, stop = false;
+    cnt.scans++;
+    while (!stop) {
+        int s = pq_pop(q, rv);
+        if (s < 0) break;
+        int x = tab.vertex(s);
+        int rx = rv[s];
+        __syncwarp();
+        int old = 0;
+        if (lane == 0) {
+            rv[s] = kDone;
+            old = atomicCAS(&A.T[x], 0, sid);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old != 0) {
+            cnt.black++;
+            continue;
+        }
+        long long L = 0, dx = 0;
+        int a0 = 0, a1 = 0;
+        if (lane == 0) {
+            A.order[x] = nS;
+            L = ld_volatile_i64(&A.st->lam);
+            a0 = A.g.rp[x];
+            a1 = A.g.rp[x + 1];
+            dx = A.g.deg[x];
+        }
+        L = __shfl_sync(0xffffffffu, L, 0);
+        dx = __shfl_sync(0xffffffffu, dx, 0);
+        a0 = __shfl_sync(0xffffffffu, a0, 0);
+        a1 = __shfl_sync(0xffffffffu, a1, 0);
+        ++nS;
+        if (rx >= kSat) alpha_ok = false;
+        alpha += dx - 2LL * rx;
+        if (alpha_ok && nS < n && alpha < L) {
+            if (lane == 0) atomicMin(&A.st->lam, alpha);
+            if (alpha < best) { best = alpha; best_len = nS; }
+            L = alpha;
+        }
+        cnt.verts++;
+        cnt.arcs += a1 - a0;
+        for (int i0 = a0; i0 < a1; i0 += 32) {
+            int i = i0 + lane;
+            bool v = i < a1;
+            int y = 0, c = 0;
+            if (v) {
+                int2 e = A.g.adj[i];
+                y = e.x;
+                c = e.y;
+            }
+            int s2 = v ? tab.find(y) : -1;
+            if (__any_sync(0xffffffffu, v && s2 < 0)) {
+                alpha_ok = false;
+                stop = true;
+            }
+            bool push = false;
+            int kn = 0;
+            if (s2 >= 0) {
+                int r_old = rv[s2];
+                if (r_old != kDone) {
+                    int r_new = sat_add(r_old, c);
+                    rv[s2] = r_new;
+                    // a certificate q = min(r, C) can only vouch for bounds <= C
+                    if ((long long)r_old < L && L <= (long long)r_new && L <= (long long)C) {
+                        if (uf_union(A.par, x, y)) cnt.unions++;
+                    }
+                    int ko = r_old < C ? r_old : C;
+                    kn = r_new < C ? r_new : C;
+                    push = r_old == 0 || q.bucket(kn) != q.bucket(ko);
+                }
+            }
+            if (!pq_push(q, push, s2, kn)) {
+                if constexpr (HASHED) {
+                    pq_rebuild(q, *reinterpret_cast<ScanSmem<Q::kHC, Q::kNB> *>(smem_for_gc));
+                } else {
+                    // the dense pool holds one entry per arc: cannot overflow
+                    stop = true;
+                    alpha_ok = false;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        A.rec_alpha[sid] = best;
+        A.rec_len[sid] = best_len;
+    }
+}
+
+template <int HC_, int NB_>
+struct SmemQ : BucketQ<unsigned short, NB_> {
+    static constexpr int kHC = HC_;
+    static constexpr int kNB = NB_;
+};
+
+template <int WPB, int HC, int NB>
+__global__ void __launch_bounds__(WPB * 32)
+k_capforest(ScanArgs A, int fifo) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    ScanSmem<HC, NB> &sm = reinterpret_cast<ScanSmem<HC, NB> *>(smem_raw)[threadIdx.x >> 5];
+    HashTable<HC, NB> tab{&sm, A.limit};
+    SmemQ<HC, NB> q;
+    q.head = sm.head;
+    q.tail = sm.tail;
+    q.bits = sm.bits;
+    q.eslot = sm.eslot;
+    q.enext = sm.enext;
+    q.top = &sm.top;
+    q.cap = 2 * HC;
+    q.fifo = fifo != 0;
+    Counters cnt;
+    const u64 n = (u64)A.g.n;
+    while (true) {
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd(&A.st->cursor, 32ULL);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        u64 idx = base + lane;
+        int v = -1;
+        bool cand = false;
+        if (idx < n) {
+            v = (int)((A.perm_a * idx + A.perm_b) % n);
+            cand = *(volatile int *)&A.T[v] == 0;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+            int l = __ffs(m) - 1;
+            m &= m - 1;
+            int start = __shfl_sync(0xffffffffu, v, l);
+            int t = 0;
+            long long L = 0;
+            if (lane == 0) {
+                t = *(volatile int *)&A.T[start];
+                L = ld_volatile_i64(&A.st->lam);
+            }
+            t = __shfl_sync(0xffffffffu, t, 0);
+            L = __shfl_sync(0xffffffffu, L, 0);
+            if (t != 0 || L <= 0) continue;
+            int sid = 0;
+            if (lane == 0) sid = atomicAdd(&A.st->scan_ids, 1) + 1;
+            sid = __shfl_sync(0xffffffffu, sid, 0);
+            // reset the warp's table and queue
+            for (int i = lane; i < HC; i += 32) sm.key[i] = -1;
+            for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
+            if (lane < NB / 32) sm.bits[lane] = 0;
+            if (lane == 0) { sm.top = 0; sm.used = 0; }
+            __syncwarp();
+            q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
+            q.coarse = q.C + 1 > NB;
+            scan_one<HashTable<HC, NB>, SmemQ<HC, NB>, true>(A, tab, q, start, sid, cnt, &sm);
+        }
+    }
+    // flush counters: unions are per lane, the rest are warp-uniform
+    long long un = cnt.unions;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), (unsigned long long)un);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)cnt.arcs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)cnt.verts);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->blacklisted), (unsigned long long)cnt.black);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), (unsigned long long)cnt.scans);
+    }
+}
+
+// full scan (Alg. 3): one warp, dense r in global memory, queue pool in
+// global memory with one entry per possible push
+constexpr int kFullNB = 1024;
+
+__global__ void __launch_bounds__(32)
+k_capforest_full(ScanArgs A, int start, int *r, int *eslot, int *enext, int pool_cap, int fifo) {
+    __shared__ int head[kFullNB];
+    __shared__ int tail[kFullNB];
+    __shared__ u32 bits[kFullNB / 32];
+    __shared__ int top;
+    const int lane = threadIdx.x & 31;
+    for (int b = lane; b < kFullNB; b += 32) { head[b] = -1; tail[b] = -1; }
+    bits[lane] = 0;
+    if (lane == 0) top = 0;
+    __syncwarp();
+    long long L = ld_volatile_i64(&A.st->lam);
+    if (L <= 0) return;
+    BucketQ<int, kFullNB> q;
+    q.head = head;
+    q.tail = tail;
+    q.bits = bits;
+    q.eslot = eslot;
+    q.enext = enext;
+    q.top = &top;
+    q.cap = pool_cap;
+    q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
+    q.coarse = q.C + 1 > kFullNB;
+    q.fifo = fifo != 0;
+    DenseTable tab{r};
+    Counters cnt;
+    int sid = 1;
+    if (lane == 0) atomicAdd(&A.st->scan_ids, 1);
+    scan_one<DenseTable, BucketQ<int, kFullNB>, false>(A, tab, q, start, sid, cnt, nullptr);
+    long long un = cnt.unions;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), (unsigned long long)un);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)cnt.arcs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)cnt.verts);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), 1ULL);
+    }
+}
+
+// smallest scan id whose best alpha equals lambda-hat
+__global__ void k_best_scan(const i64 *__restrict__ rec_alpha, const int *__restrict__ rec_len, Status *st) {
+    const int ns = st->scan_ids;
+    const long long lam = st->lam;
+    for (int s = 1 + blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += gridDim.x * blockDim.x)
+        if (rec_alpha[s] == lam) atomicMin(&st->best_scan, s);
+}
+
+__global__ void k_best_len(const int *__restrict__ rec_len, Status *st) {
+    st->best_len = st->best_scan < INT_MAX ? rec_len[st->best_scan] : 0;
+    if (st->best_scan == INT_MAX) st->best_scan = -1;
+}
+
+__global__ void k_scan_reset(Status *st) {
+    st->cursor = 0;
+    st->scan_ids = 0;
+    st->best_scan = INT_MAX;
+    st->best_len = 0;
+}
+
+__global__ void k_fill_i32(int *a, int n, int v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+template <int WPB, int HC, int NB>
+static int launch_parallel(const ScanArgs &A, int fifo, int warps_wanted, cudaStream_t s) {
+    const size_t smem = (size_t)WPB * sizeof(ScanSmem<HC, NB>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        MC_CUDA(cudaFuncSetAttribute(k_capforest<WPB, HC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr_set = true;
+    }
+    int per_sm = 0;
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest<WPB, HC, NB>, WPB * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    int blocks = per_sm * num_sms();
+    if (warps_wanted > 0) {
+        int b = (warps_wanted + WPB - 1) / WPB;
+        if (b < blocks) blocks = b;
+    }
+    // no more warps than start candidates
+    int maxb = (A.g.n + 32 * WPB - 1) / (32 * WPB);
+    if (maxb < 1) maxb = 1;
+    if (blocks > maxb) blocks = maxb;
+    ++::mc::g_launches; k_capforest<WPB, HC, NB><<<blocks, WPB * 32, smem, s>>>(A, fifo);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+static u64 gcd_u64(u64 a, u64 b) {
+    while (b) { u64 t = a % b; a = b; b = t; }
+    return a;
+}
+
+static ScanArgs make_args(const DevGraph &g, Work &w, const ScanConfig &cfg) {
+    ScanArgs A;
+    A.g = g;
+    A.par = w.par;
+    A.T = w.T;
+    A.order = w.order;
+    A.st = w.st;
+    A.rec_alpha = w.rec_alpha;
+    A.rec_len = w.rec_len;
+    const u64 n = (u64)(g.n > 0 ? g.n : 1);
+    u64 h = (cfg.seed ^ 0x5851F42D4C957F2DULL) + (u64)cfg.round * 0x9E3779B97F4A7C15ULL;
+    h ^= h >> 29; h *= 0xBF58476D1CE4E5B9ULL; h ^= h >> 32;
+    u64 a = (h % n) | 1;
+    while (gcd_u64(a, n) != 1) a = (a + 2) % n == 0 ? 1 : (a + 2) % n;
+    if (n == 1) a = 1;
+    A.perm_a = a % n == 0 ? 1 : a;
+    A.perm_b = (h >> 17) % n;
+    A.limit = 0;
+    return A;
+}
+
+int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s) {
+    MC_CUDA(cudaMemsetAsync(w.T, 0, sizeof(int) * (size_t)g.n, s));
+    ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
+    ScanArgs A = make_args(g, w, cfg);
+    int budget = cfg.budget > 0 ? cfg.budget : 768;
+    constexpr int WPB = 4;
+    int rc;
+    if (budget <= 384 - 32) {
+        A.limit = budget;
+        rc = launch_parallel<WPB, 512, 256>(A, cfg.pq_fifo, cfg.warps, s);
+    } else if (budget <= 768) {
+        A.limit = budget;
+        rc = launch_parallel<WPB, 1024, 256>(A, cfg.pq_fifo, cfg.warps, s);
+    } else {
+        A.limit = budget < 1536 ? budget : 1536;
+        rc = launch_parallel<WPB, 2048, 256>(A, cfg.pq_fifo, cfg.warps, s);
+    }
+    if (rc != MC_OK) return rc;
+    ++::mc::g_launches; k_best_scan<<<64, 256, 0, s>>>(w.rec_alpha, w.rec_len, w.st);
+    ++::mc::g_launches; k_best_len<<<1, 1, 0, s>>>(w.rec_len, w.st);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s) {
+    MC_CUDA(cudaMemsetAsync(w.T, 0, sizeof(int) * (size_t)g.n, s));
+    MC_CUDA(cudaMemsetAsync(w.fb_r, 0, sizeof(int) * (size_t)g.n, s));
+    ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
+    ScanArgs A = make_args(g, w, cfg);
+    const int start = (int)(A.perm_b % (u64)(g.n > 0 ? g.n : 1));
+    const i64 pool = g.arcs + 2;
+    int *eslot = reinterpret_cast<int *>(w.fb_pool);
+    int *enext = eslot + pool;
+    ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, w.fb_r, eslot, enext, (int)pool, cfg.pq_fifo);
+    ++::mc::g_launches; k_best_scan<<<1, 32, 0, s>>>(w.rec_alpha, w.rec_len, w.st);
+    ++::mc::g_launches; k_best_len<<<1, 1, 0, s>>>(w.rec_len, w.st);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+}  // namespace mc

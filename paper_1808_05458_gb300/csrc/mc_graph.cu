@@ -1,0 +1,537 @@
+// mc_graph.cu -- graph ingest, contraction and bookkeeping kernels.
+//
+// Contraction (Sec. 2.1; Sec. 3.2 "Parallel Graph Contraction"): the paper
+// builds G_C with a concurrent hash table keyed by the block ids of each
+// edge.  Here the same G_C comes from
+//   flatten the union-find -> number the blocks by a scan (block id order =
+//   smallest member) -> emit one (block(u), block(v), c) arc per arc whose
+//   ends fall in different blocks -> LSD radix sort on the packed key ->
+//   segmented sum of parallel arcs -> CSR offsets, degrees and the minimum
+//   degree (the lambda-hat update of Sec. 3.2).
+// Merged weights are clamped to the current lambda-hat before the int32
+// store: an edge of weight >= lambda-hat already certifies every cut through
+// it is >= lambda-hat, so the clamp changes no cut below lambda-hat.
+#include <cstdio>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+constexpr int kThreads = 256;
+
+static int grid_for(i64 n, int threads = kThreads) {
+    i64 b = (n + threads - 1) / threads;
+    i64 cap = (i64)num_sms() * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// -------------------------------------------------------------- alloc ----
+int graph_alloc(DevGraph &g, i64 n, i64 arcs, cudaStream_t s) {
+    MC_TRY(dev_alloc_n(&g.rp, (size_t)n + 1, s));
+    MC_TRY(dev_alloc_n(&g.src, (size_t)arcs, s));
+    MC_TRY(dev_alloc_n(&g.adj, (size_t)arcs, s));
+    MC_TRY(dev_alloc_n(&g.deg, (size_t)n, s));
+    return MC_OK;
+}
+
+void graph_free(DevGraph &g, cudaStream_t s) {
+    dev_free(g.rp, s); dev_free(g.src, s); dev_free(g.adj, s); dev_free(g.deg, s);
+    g = DevGraph();
+}
+
+int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
+    w.cap_n = n0;
+    w.cap_arcs = arcs0;
+    i64 a = arcs0 > n0 ? arcs0 : n0;
+    MC_TRY(dev_alloc_n(&w.par, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.lab, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.T, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.order, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.cnt, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.orig, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.scan_tmp, scan_tmp_words(a * 256), s));
+    MC_TRY(dev_alloc_n(&w.keysA, (size_t)a, s));
+    MC_TRY(dev_alloc_n(&w.keysB, (size_t)a, s));
+    MC_TRY(dev_alloc_n(&w.valsA, (size_t)a, s));
+    MC_TRY(dev_alloc_n(&w.valsB, (size_t)a, s));
+    MC_TRY(dev_alloc_n(&w.radix_tmp, radix_tmp_words(a), s));
+    MC_TRY(dev_alloc_n(&w.rec_alpha, (size_t)n0 + 1, s));
+    MC_TRY(dev_alloc_n(&w.rec_len, (size_t)n0 + 1, s));
+    MC_TRY(dev_alloc_n(&w.fb_r, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.fb_pool, 2 * ((size_t)a + 64), s));
+    MC_TRY(dev_alloc_n(&w.best_side, (size_t)(n0 + 31) / 32, s));
+    MC_TRY(dev_alloc_n(&w.st, 1, s));
+    MC_CUDA(cudaMallocHost(reinterpret_cast<void **>(&w.h_st), sizeof(Status)));
+    return MC_OK;
+}
+
+void work_free(Work &w, cudaStream_t s) {
+    void *ps[] = {w.par, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
+                  w.valsA, w.valsB, w.radix_tmp, w.rec_alpha, w.rec_len, w.fb_r, w.fb_pool,
+                  w.best_side, w.st};
+    for (void *p : ps) dev_free(p, s);
+    if (w.h_st) cudaFreeHost(w.h_st);
+    w = Work();
+}
+
+// ------------------------------------------------------------ helpers ----
+__global__ void k_iota(int *a, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+int union_find_init(int *par, int n, cudaStream_t s) {
+    ++::mc::g_launches; k_iota<<<grid_for(n), kThreads, 0, s>>>(par, n);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+// flatten: par[v] = root(v); cnt[v] = (v is a root)
+__global__ void k_flatten(int *par, int *cnt, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int r = uf_find(par, v);
+        cnt[v] = (r == v);
+        par[v] = r;
+    }
+}
+
+// lab[v] = lab[root(v)]; roots already hold their new id from the scan
+__global__ void k_relabel(const int *__restrict__ par, int *lab, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int r = par[v];
+        if (r != v) lab[v] = lab[r];
+    }
+}
+
+// ------------------------------------------------------------- emitting ---
+// one (block(u), block(v), c) arc per arc with different blocks; warp-wide
+// compaction through a single counter
+__global__ void k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs,
+                       const int *__restrict__ lab, u64 nc, u64 *__restrict__ keys,
+                       int *__restrict__ vals, u64 *counter) {
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < arcs; i0 += stride) {
+        i64 i = i0 + lane;
+        bool ok = i < arcs;
+        int a = 0, b = 0, c = 0;
+        if (ok) {
+            int2 e = adj[i];
+            a = lab[src[i]];
+            b = lab[e.x];
+            c = e.y;
+            ok = a != b;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (!m) continue;
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd(counter, (u64)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+            u64 pos = base + __popc(m & ((1u << lane) - 1u));
+            keys[pos] = (u64)a * nc + (u64)b;
+            vals[pos] = c;
+        }
+    }
+}
+
+// raw input arcs: validate and emit (u, v, c) for u != v, c > 0
+__global__ void k_emit_raw(const int *__restrict__ rp, const int *__restrict__ col,
+                           const int *__restrict__ w, int n, i64 arcs, u64 *__restrict__ keys,
+                           int *__restrict__ vals, u64 *counter, int *err) {
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < arcs; i0 += stride) {
+        i64 i = i0 + lane;
+        bool ok = i < arcs;
+        int u = 0, v = 0, c = 0;
+        if (ok) {
+            // source row by binary search: largest u with rp[u] <= i
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((i64)rp[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            u = lo;
+            v = col[i];
+            c = w[i];
+            if (v < 0 || v >= n) { atomicOr(err, kErrRange); ok = false; }
+            else if (c < 0) { atomicOr(err, kErrNegW); ok = false; }
+            else ok = (u != v) && (c > 0);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (!m) continue;
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd(counter, (u64)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+            u64 pos = base + __popc(m & ((1u << lane) - 1u));
+            keys[pos] = (u64)u * (u64)n + (u64)v;
+            vals[pos] = c;
+        }
+    }
+}
+
+__global__ void k_check_rp(const int *__restrict__ rp, int n, int *err) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (rp[v + 1] < rp[v]) atomicOr(err, kErrRange);
+        if (v == 0 && rp[0] != 0) atomicOr(err, kErrRange);
+    }
+}
+
+// ------------------------------------------------------ segmented sum ----
+__global__ void k_heads(const u64 *__restrict__ keys, i64 m, int *__restrict__ flag) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (i64)gridDim.x * blockDim.x)
+        flag[i] = (i == 0) || (keys[i] != keys[i - 1]);
+}
+
+// sum the weights of each run of equal keys into acc[j] (int64), write the
+// run's (src, col); `ex` is the exclusive scan of the head flags
+__global__ void k_seg_sum(const u64 *__restrict__ keys, const int *__restrict__ vals,
+                          const int *__restrict__ ex, i64 m, u64 nc, u64 *__restrict__ acc,
+                          int *__restrict__ osrc, int2 *__restrict__ oadj) {
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < m; i0 += stride) {
+        i64 i = i0 + lane;
+        bool ok = i < m;
+        u64 key = ok ? keys[i] : ~0ULL;
+        bool head = ok && (i == 0 || keys[i - 1] != key);
+        long long j = ok ? (long long)ex[i] + (head ? 1 : 0) - 1 : -1 - lane;
+        long long s = ok ? vals[i] : 0;
+        // segmented reduction toward the first lane of each run in this warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_down_sync(0xffffffffu, s, o);
+            long long jo = __shfl_down_sync(0xffffffffu, j, o);
+            if (lane + o < 32 && jo == j) s += t;
+        }
+        long long jp = __shfl_up_sync(0xffffffffu, j, 1);
+        bool first = ok && (lane == 0 || jp != j);
+        if (first) atomicAdd(&acc[j], (u64)s);
+        if (head) {
+            osrc[j] = (int)(key / nc);
+            oadj[j].x = (int)(key % nc);
+        }
+    }
+}
+
+// clamp the summed weights, store them, and accumulate degrees
+__global__ void k_finalize(const u64 *__restrict__ acc, i64 m, i64 clamp, const int *__restrict__ osrc,
+                           int2 *__restrict__ oadj, unsigned long long *deg, int *err) {
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < m; i0 += stride) {
+        i64 i = i0 + lane;
+        bool ok = i < m;
+        long long s = ok ? (long long)acc[i] : 0;
+        if (s > clamp) s = clamp;
+        if (ok && s > kInt32Max) { atomicOr(err, kErrOverflow); s = kInt32Max; }
+        int a = ok ? osrc[i] : -1 - lane;
+        if (ok) oadj[i].y = (int)s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_down_sync(0xffffffffu, s, o);
+            int ao = __shfl_down_sync(0xffffffffu, a, o);
+            if (lane + o < 32 && ao == a) s += t;
+        }
+        int ap = __shfl_up_sync(0xffffffffu, a, 1);
+        if (ok && (lane == 0 || ap != a)) atomicAdd(&deg[a], (unsigned long long)s);
+    }
+}
+
+// CSR offsets from the sorted sources
+__global__ void k_rowptr(const int *__restrict__ osrc, i64 m, int nc, int *__restrict__ rp) {
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j <= m; j += (i64)gridDim.x * blockDim.x) {
+        int prev = j == 0 ? -1 : osrc[j - 1];
+        int cur = j == m ? nc : osrc[j];
+        for (int x = prev + 1; x <= cur && x <= nc; ++x) rp[x] = (int)j;
+        if (j == m && m == 0) rp[nc] = 0;
+    }
+}
+
+// ------------------------------------------------------------ min degree --
+__global__ void k_min_deg(const i64 *__restrict__ deg, int n, Status *st) {
+    __shared__ long long red[kThreads / 32];
+    long long best = LLONG_MAX;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        best = min(best, deg[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kThreads / 32; ++k) best = min(best, red[k]);
+        atomicMin(&st->mindeg, best);
+    }
+}
+
+__global__ void k_argmin_deg(const i64 *__restrict__ deg, int n, Status *st) {
+    const long long md = st->mindeg;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (deg[v] == md) atomicMin(&st->argmin, v);
+}
+
+__global__ void k_reset_min(Status *st) {
+    st->mindeg = LLONG_MAX;
+    st->argmin = INT_MAX;
+}
+
+int min_degree(const DevGraph &g, Work &w, cudaStream_t s) {
+    ++::mc::g_launches; k_reset_min<<<1, 1, 0, s>>>(w.st);
+    ++::mc::g_launches; k_min_deg<<<grid_for(g.n), kThreads, 0, s>>>(g.deg, g.n, w.st);
+    ++::mc::g_launches; k_argmin_deg<<<grid_for(g.n), kThreads, 0, s>>>(g.deg, g.n, w.st);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+__global__ void k_zero_count(Status *st) {
+    st->count = 0;
+    st->count2 = 0;
+}
+
+static int bits_for(u64 x) {
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+// sorted (keys, vals) of m arcs over nc vertices -> out graph (+ degrees)
+static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cudaStream_t s) {
+    bool in_b = false;
+    MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, m, bits_for((u64)nc * (u64)nc - 1),
+                            w.radix_tmp, w.scan_tmp, &in_b, s));
+    u64 *keys = in_b ? w.keysB : w.keysA;
+    int *vals = in_b ? w.valsB : w.valsA;
+    int *flags = in_b ? w.valsA : w.valsB;      // free int32 buffer
+    u64 *acc = in_b ? w.keysA : w.keysB;        // free 64-bit buffer
+    int *d_total = reinterpret_cast<int *>(&w.st->count2);
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    if (m > 0) {
+        ++::mc::g_launches; k_heads<<<grid_for(m), kThreads, 0, s>>>(keys, m, flags);
+        MC_TRY(exclusive_scan_i32(flags, flags, m, d_total, w.scan_tmp, s));
+    }
+    MC_TRY(status_read(w, s));
+    const i64 mu = m > 0 ? (i64)(int)w.h_st->count2 : 0;
+    out.n = nc;
+    out.arcs = mu;
+    MC_CUDA(cudaMemsetAsync(out.deg, 0, sizeof(i64) * (size_t)nc, s));
+    if (mu > 0) {
+        MC_CUDA(cudaMemsetAsync(acc, 0, sizeof(u64) * (size_t)mu, s));
+        ++::mc::g_launches; k_seg_sum<<<grid_for(m), kThreads, 0, s>>>(keys, vals, flags, m, (u64)nc, acc, out.src,
+                                                   out.adj);
+        ++::mc::g_launches; k_finalize<<<grid_for(mu), kThreads, 0, s>>>(acc, mu, clamp, out.src, out.adj,
+                                                     reinterpret_cast<unsigned long long *>(out.deg),
+                                                     &w.st->err);
+    }
+    ++::mc::g_launches; k_rowptr<<<grid_for(mu + 1), kThreads, 0, s>>>(out.src, mu, nc, out.rp);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool flatten, int nc,
+                   cudaStream_t s) {
+    const int n = in.n;
+    if (flatten) {
+        ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.cnt, n);
+        int *d_total = reinterpret_cast<int *>(&w.st->count);
+        ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+        MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, d_total, w.scan_tmp, s));
+        ++::mc::g_launches; k_relabel<<<grid_for(n), kThreads, 0, s>>>(w.par, w.lab, n);
+        MC_TRY(status_read(w, s));
+        nc = (int)w.h_st->count;
+    }
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    ++::mc::g_launches; k_emit<<<grid_for(in.arcs), kThreads, 0, s>>>(in.src, in.adj, in.arcs, w.lab, (u64)nc, w.keysA,
+                                                  w.valsA, reinterpret_cast<u64 *>(&w.st->count));
+    MC_CUDA(cudaGetLastError());
+    MC_TRY(status_read(w, s));
+    const i64 m = w.h_st->count;
+    return build_from_pairs(m, nc, clamp, out, w, s);
+}
+
+// binary search in the sorted row of v for u; mirror weight or -1
+__device__ __forceinline__ int find_arc(const int *rp, const int2 *adj, int v, int u) {
+    int lo = rp[v], hi = rp[v + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int x = adj[mid].x;
+        if (x == u) return adj[mid].y;
+        if (x < u) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+__global__ void k_check_sym(const DevGraph g, int *err) {
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
+        int u = g.src[j];
+        int2 e = g.adj[j];
+        if (find_arc(g.rp, g.adj, e.x, u) != e.y) atomicOr(err, kErrAsym);
+    }
+}
+
+__global__ void k_clear_err(Status *st) { st->err = 0; }
+
+int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym, DevGraph &out,
+                 Work &wk, cudaStream_t s) {
+    ++::mc::g_launches; k_clear_err<<<1, 1, 0, s>>>(wk.st);
+    ++::mc::g_launches; k_check_rp<<<grid_for(n), kThreads, 0, s>>>(rp, n, &wk.st->err);
+    MC_TRY(status_read(wk, s));
+    if (wk.h_st->err) return MC_EINVAL;
+    int arcs_raw = 0;
+    MC_CUDA(cudaMemcpyAsync(&arcs_raw, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (arcs_raw < 0 || (i64)arcs_raw > wk.cap_arcs) return MC_EINVAL;
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
+    ++::mc::g_launches; k_emit_raw<<<grid_for(arcs_raw), kThreads, 0, s>>>(rp, col, w, n, arcs_raw, wk.keysA, wk.valsA,
+                                                       reinterpret_cast<u64 *>(&wk.st->count),
+                                                       &wk.st->err);
+    MC_CUDA(cudaGetLastError());
+    MC_TRY(status_read(wk, s));
+    if (wk.h_st->err) return MC_EINVAL;
+    const i64 m = wk.h_st->count;
+    MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s));
+    if (check_sym && out.arcs > 0) {
+        ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err);
+        MC_CUDA(cudaGetLastError());
+    }
+    MC_TRY(status_read(wk, s));
+    if (wk.h_st->err & kErrOverflow) return MC_EOVERFLOW;
+    if (wk.h_st->err) return MC_EINVAL;
+    return MC_OK;
+}
+
+// ------------------------------------------------- connected components ---
+__global__ void k_cc_union(const DevGraph g, int *par) {
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
+        int u = g.src[j], v = g.adj[j].x;
+        if (u < v) uf_union(par, u, v);
+    }
+}
+
+int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s) {
+    MC_TRY(union_find_init(w.par, g.n, s));
+    if (g.arcs > 0) { ++::mc::g_launches; k_cc_union<<<grid_for(g.arcs), kThreads, 0, s>>>(g, w.par); }
+    ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.cnt, g.n);
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    MC_TRY(exclusive_scan_i32(w.cnt, w.lab, g.n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
+    MC_TRY(status_read(w, s));
+    *ncomp = (int)w.h_st->count;
+    return MC_OK;
+}
+
+// ------------------------------------------------------------ side bits ---
+// bit v of the side bitmap, one warp per 32 vertices
+template <class F>
+__global__ void k_side_bits(int n0, u32 *bits, F f) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (n0 + 31) / 32;
+    for (int wd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wd < nw; wd += (gridDim.x * blockDim.x) >> 5) {
+        int v = wd * 32 + lane;
+        bool b = v < n0 && f(v);
+        unsigned m = __ballot_sync(0xffffffffu, b);
+        if (lane == 0) bits[wd] = m;
+    }
+}
+
+struct SideVertex {
+    const int *orig;
+    int vertex;
+    __device__ bool operator()(int v) const { return orig[v] == vertex; }
+};
+struct SideScan {
+    const int *orig, *T, *order;
+    int scan, len;
+    __device__ bool operator()(int v) const {
+        int c = orig[v];
+        return T[c] == scan && order[c] < len;
+    }
+};
+struct SideComp {
+    const int *par;
+    __device__ bool operator()(int v) const { return par[v] != par[0]; }
+};
+
+static int side_grid(int n0) { return grid_for(((i64)n0 + 31) / 32 * 32); }
+
+int side_from_vertex(Work &w, int n0, int vertex, cudaStream_t s) {
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideVertex{w.orig, vertex});
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+int side_from_scan(Work &w, int n0, int scan, int len, cudaStream_t s) {
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideScan{w.orig, w.T, w.order, scan, len});
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+int side_from_component(Work &w, int n0, cudaStream_t s) {
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideComp{w.par});
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+__global__ void k_orig_update(int *orig, const int *__restrict__ lab, int n0) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n0; v += gridDim.x * blockDim.x)
+        orig[v] = lab[orig[v]];
+}
+
+int orig_update(Work &w, int n0, cudaStream_t s) {
+    ++::mc::g_launches; k_orig_update<<<grid_for(n0), kThreads, 0, s>>>(w.orig, w.lab, n0);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+}  // namespace mc
+
+namespace mc {
+
+int flatten_labels(Work &w, int n, cudaStream_t s) {
+    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.cnt, n);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+__global__ void k_round_reset(Status *st, long long lam) {
+    st->lam = lam;
+    st->unions = 0;
+    st->scanned_arcs = 0;
+    st->scanned_verts = 0;
+    st->scans = 0;
+    st->blacklisted = 0;
+    st->err = 0;
+}
+
+int round_reset(Work &w, i64 lam, cudaStream_t s) {
+    ++::mc::g_launches; k_round_reset<<<1, 1, 0, s>>>(w.st, lam);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+// canonical polarity: vertex 0 on side 0; clear the bits past n0
+__global__ void k_side_canon(u32 *bits, int n0) {
+    const int nw = (n0 + 31) / 32;
+    const bool flip = bits[0] & 1u;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
+        u32 v = flip ? ~bits[i] : bits[i];
+        if (i == nw - 1 && (n0 & 31)) v &= (1u << (n0 & 31)) - 1u;
+        bits[i] = v;
+    }
+}
+
+int side_canon(Work &w, int n0, cudaStream_t s) {
+    // one block: bits[0] is read by every thread before any write
+    ++::mc::g_launches; k_side_canon<<<1, 1024, 0, s>>>(w.best_side, n0);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+int iota_i32(int *a, int n, cudaStream_t s) {
+    ++::mc::g_launches; k_iota<<<grid_for(n), kThreads, 0, s>>>(a, n);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+}  // namespace mc

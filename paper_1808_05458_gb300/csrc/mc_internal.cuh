@@ -1,0 +1,242 @@
+// mc_internal.cuh -- shared declarations of the libmincut CUDA path.
+//
+// Device layout of a graph (one GPU, HBM resident):
+//   rp   int32[n+1]   CSR row offsets
+//   src  int32[arcs]  source vertex of each arc (rows are contiguous, sorted)
+//   adj  int2[arcs]   {neighbour, weight} of each arc, rows sorted by neighbour
+//   deg  int64[n]     weighted degree (Sec. 2.1)
+// Both directions of every undirected edge are stored.  Weights are int32,
+// degrees, cut values and lambda-hat are int64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+
+#include <string>
+
+#include "mc.h"
+
+namespace mc {
+
+using i64 = long long;
+using u64 = unsigned long long;
+using u32 = unsigned int;
+
+constexpr int kWarp = 32;
+constexpr i64 kInt32Max = 2147483647LL;
+
+// number of kernels launched by this host thread (reported in mc_stats)
+extern thread_local long long g_launches;
+
+// ---------------------------------------------------------------- errors --
+void set_cuda_error(cudaError_t e, const char *what);
+void set_error_detail(const char *msg);
+
+#define MC_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) {                              \
+            ::mc::set_cuda_error(_e, #call);                  \
+            return MC_ECUDA;                                  \
+        }                                                     \
+    } while (0)
+
+#define MC_TRY(expr)                 \
+    do {                             \
+        int _rc = (expr);            \
+        if (_rc != MC_OK) return _rc; \
+    } while (0)
+
+// ------------------------------------------------------------- allocation --
+// Device memory comes from the stream-ordered allocator (cudaMallocAsync) on
+// the graph's stream; buffers live as long as their owning mc_graph.
+int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+template <class T>
+int dev_alloc_n(T **p, size_t n, cudaStream_t s) {
+    return dev_alloc(reinterpret_cast<void **>(p), (n ? n : 1) * sizeof(T), s);
+}
+
+// ------------------------------------------------------------------ graph --
+struct DevGraph {
+    int n = 0;
+    i64 arcs = 0;
+    int *rp = nullptr;
+    int *src = nullptr;
+    int2 *adj = nullptr;
+    i64 *deg = nullptr;
+};
+
+// Device-resident status block, read back once per phase.
+struct Status {
+    i64 lam;            // lambda-hat (atomicMin target)
+    i64 unions;         // successful unions this round
+    i64 scanned_arcs;   // arcs read by CAPFOREST
+    i64 scanned_verts;  // vertices scanned by CAPFOREST
+    i64 scans;          // scans started
+    i64 blacklisted;    // pops that hit another scan's vertex
+    i64 count;          // generic counter (emitted arcs, roots, ...)
+    i64 count2;         // second generic counter
+    i64 mindeg;         // minimum weighted degree of the current graph
+    int argmin;         // smallest vertex with that degree
+    int err;            // error bits (kErr*)
+    u64 cursor;         // start-vertex cursor of the concurrent scans
+    int scan_ids;       // scan id counter
+    int best_scan;      // scan whose alpha set lambda-hat (or -1)
+    int best_len;       // prefix length of that scan
+    int pad;
+};
+
+constexpr int kErrAsym = 1;       // asymmetric input
+constexpr int kErrRange = 2;      // neighbour out of range / bad offsets
+constexpr int kErrNegW = 4;       // negative weight
+constexpr int kErrOverflow = 8;   // weight or degree overflow
+constexpr int kErrNoProgress = 16;
+
+// --------------------------------------------------------------- launches --
+int num_sms();
+
+// device-wide exclusive scan of int32 counts into int32 offsets; *d_total
+// receives the sum (may be nullptr).  tmp must hold scan_tmp_words(n) ints.
+size_t scan_tmp_words(i64 n);
+int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp,
+                       cudaStream_t s);
+
+// LSD radix sort of (key, value) pairs on the low `bits` bits of the keys.
+// Buffers A hold the input; the result ends in A or B (returned via *in_b).
+// tmp must hold radix_tmp_words(n) uint32.
+size_t radix_tmp_words(i64 n);
+int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int bits,
+                     u32 *tmp, int *scan_tmp, bool *in_b, cudaStream_t s);
+
+// Contraction workspace.
+struct Work {
+    // per-vertex (sized n0)
+    int *par = nullptr;      // union-find parents
+    int *lab = nullptr;      // relabel map
+    int *T = nullptr;        // scan owner of each vertex (0 = unvisited)
+    int *order = nullptr;    // visit index inside the owning scan
+    int *cnt = nullptr;      // per-vertex counts / flags
+    int *orig = nullptr;     // original vertex -> current vertex
+    int *scan_tmp = nullptr;
+    // per-arc (sized arcs0)
+    u64 *keysA = nullptr, *keysB = nullptr;
+    int *valsA = nullptr, *valsB = nullptr;
+    u32 *radix_tmp = nullptr;
+    // per-scan records
+    i64 *rec_alpha = nullptr;
+    int *rec_len = nullptr;
+    // fallback scan state (dense, sized n0 / arcs0)
+    int *fb_r = nullptr;
+    u32 *fb_pool = nullptr;
+    // side bitmap of the best cut so far (original ids)
+    u32 *best_side = nullptr;
+    // status
+    Status *st = nullptr;
+    Status *h_st = nullptr;  // pinned mirror
+    i64 cap_n = 0, cap_arcs = 0;
+};
+
+int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s);
+void work_free(Work &w, cudaStream_t s);
+int graph_alloc(DevGraph &g, i64 n, i64 arcs, cudaStream_t s);
+void graph_free(DevGraph &g, cudaStream_t s);
+
+// read the status block back (synchronises the stream)
+int status_read(Work &w, cudaStream_t s);
+
+// ---------------------------------------------------------- path steps --
+// Sec. 2.1 contraction of `in` by union-find blocks in w.par (roots are the
+// smallest member): writes `out`, its degrees, lambda-hat update candidates
+// (st->mindeg / st->argmin) and w.lab (old vertex -> new vertex).  Merged
+// weights are clamped to `clamp` (> 0).  If `flatten` is false, w.lab holds
+// ready labels in [0, nc) with nc given.
+int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool flatten, int nc,
+                   cudaStream_t s);
+
+// canonicalise raw CSR arrays (device) into `out` (drops self-loops / zero
+// weights, sums parallel arcs, sorts rows); checks symmetry if asked.
+int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym,
+                 DevGraph &out, Work &wk, cudaStream_t s);
+
+int union_find_init(int *par, int n, cudaStream_t s);
+int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s);
+
+// minimum degree + smallest argmin into st->mindeg / st->argmin
+int min_degree(const DevGraph &g, Work &w, cudaStream_t s);
+
+// Padberg-Rinaldi tests 1..level against lam: unions into w.par
+int pr_tests(const DevGraph &g, Work &w, i64 lam, int level, cudaStream_t s);
+
+// concurrent capped CAPFOREST (Alg. 1): unions into w.par, alpha updates
+// into st->lam, owners in w.T / w.order, records in w.rec_*.
+struct ScanConfig {
+    int pq_fifo = 0;
+    int warps = 0;         // concurrent scan warps (0 = auto)
+    int budget = 0;        // touched-vertex budget per scan (0 = auto)
+    u64 seed = 0;
+    int round = 0;
+};
+int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
+// one full CAPFOREST scan (Alg. 3) from a start vertex, single warp
+int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
+
+// side bitmaps (original vertex ids, n0 bits)
+int side_from_vertex(Work &w, int n0, int vertex, cudaStream_t s);
+int side_from_scan(Work &w, int n0, int scan, int len, cudaStream_t s);
+int side_from_component(Work &w, int n0, cudaStream_t s);  // par = CC roots
+int orig_update(Work &w, int n0, cudaStream_t s);           // orig = lab[orig]
+
+int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int level, int budget, cudaStream_t s);
+int flatten_labels(Work &w, int n, cudaStream_t s);   // par[v] = root, labels in par
+int round_reset(Work &w, i64 lam, cudaStream_t s);    // st->lam = lam, counters = 0
+int side_canon(Work &w, int n0, cudaStream_t s);
+int iota_i32(int *a, int n, cudaStream_t s);
+const std::string &error_detail();
+
+// label propagation sweeps on g into labels (int32[n])
+int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cudaStream_t s);
+
+// ---------------------------------------------------------- device bits --
+__device__ __forceinline__ u64 splitmix64(u64 x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+// Union-find with parents always below their children (link the larger root
+// under the smaller), path halving on finds.  Safe under concurrency: only
+// roots are linked (by CAS) and halving only shortens paths to ancestors.
+__device__ __forceinline__ int uf_find(int *par, int x) {
+    volatile int *p = par;
+    while (true) {
+        int px = p[x];
+        if (px == x) return x;
+        int gx = p[px];
+        if (gx == px) return px;
+        p[x] = gx;
+        x = gx;
+    }
+}
+
+__device__ __forceinline__ bool uf_union(int *par, int a, int b) {
+    while (true) {
+        a = uf_find(par, a);
+        b = uf_find(par, b);
+        if (a == b) return false;
+        if (a > b) { int t = a; a = b; b = t; }
+        if (atomicCAS(&par[b], b, a) == b) return true;
+    }
+}
+
+__device__ __forceinline__ i64 ld_volatile_i64(const i64 *p) {
+    return *reinterpret_cast<const volatile i64 *>(p);
+}
+
+inline int div_up(i64 a, i64 b) { return (int)((a + b - 1) / b); }
+
+}  // namespace mc

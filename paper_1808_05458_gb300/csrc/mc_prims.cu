@@ -1,0 +1,280 @@
+// mc_prims.cu -- errors, allocation, device-wide scan and LSD radix sort.
+//
+// The radix sort and scan are the building blocks of the CSR rebuild by
+// "radix sort plus segmented sum" that replaces the paper's concurrent hash
+// table in parallel graph contraction (Sec. 3.2).
+#include <cstdio>
+#include <cstring>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+thread_local long long g_launches = 0;
+
+// ----------------------------------------------------------------- errors --
+static thread_local std::string g_detail;
+
+void set_cuda_error(cudaError_t e, const char *what) {
+    g_detail = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e) + " in " + what;
+}
+void set_error_detail(const char *msg) { g_detail = msg; }
+const std::string &error_detail() { return g_detail; }
+
+// ------------------------------------------------------------- allocation --
+int dev_alloc(void **p, size_t bytes, cudaStream_t) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        set_cuda_error(e, "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA;
+    }
+    return MC_OK;
+}
+
+void dev_free(void *p, cudaStream_t) {
+    if (p) cudaFree(p);
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int status_read(Work &w, cudaStream_t s) {
+    MC_CUDA(cudaMemcpyAsync(w.h_st, w.st, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+// ------------------------------------------------------------------- scan --
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan across the block; the block total goes to *total (a shared
+// variable of the caller, valid after the call)
+template <class T, int NT>
+__device__ __forceinline__ T block_excl_scan(T v, T *total) {
+    __shared__ T wsum[NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T x = lane < NT / 32 ? wsum[lane] : T(0);
+        T xs = warp_incl_scan(x);
+        if (lane < NT / 32) wsum[lane] = xs - x;
+        if (lane == NT / 32 - 1) *total = xs;
+    }
+    __syncthreads();
+    T r = wsum[wid] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_tile_reduce(const int *__restrict__ in, i64 n, int *__restrict__ part) {
+    i64 base = (i64)blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        i64 i = base + (i64)k * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    __shared__ int tot;
+    int ex = block_excl_scan<int, kScanThreads>(s, &tot);
+    (void)ex;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of part[0..nt) in place, total to *d_total
+__global__ void k_scan_parts(int *part, int nt, int *d_total) {
+    const int per = (nt + 1023) / 1024;
+    int lo = threadIdx.x * per, hi = min(nt, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += part[i];
+    __shared__ int tot;
+    int ex = block_excl_scan<int, 1024>(s, &tot);
+    for (int i = lo; i < hi; ++i) {
+        int v = part[i];
+        part[i] = ex;
+        ex += v;
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = tot;
+}
+
+__global__ void k_tile_scan(const int *__restrict__ in, int *__restrict__ out, i64 n,
+                            const int *__restrict__ part) {
+    // blocked arrangement: thread t owns items [t*ITEMS, t*ITEMS+ITEMS)
+    i64 base = (i64)blockIdx.x * kScanTile + (i64)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        i64 i = base + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    __shared__ int tot;
+    int ex = block_excl_scan<int, kScanThreads>(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        i64 i = base + k;
+        if (i < n) out[i] = ex;
+        ex += v[k];
+    }
+}
+
+size_t scan_tmp_words(i64 n) { return (size_t)div_up(n > 0 ? n : 1, kScanTile) + 32; }
+
+int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp,
+                       cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) MC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int), s));
+        return MC_OK;
+    }
+    int nt = div_up(n, kScanTile);
+    ++::mc::g_launches; k_tile_reduce<<<nt, kScanThreads, 0, s>>>(d_in, n, tmp);
+    ++::mc::g_launches; k_scan_parts<<<1, 1024, 0, s>>>(tmp, nt, d_total);
+    ++::mc::g_launches; k_tile_scan<<<nt, kScanThreads, 0, s>>>(d_in, d_out, n, tmp);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+// ------------------------------------------------------------- radix sort --
+// LSD radix sort, 8-bit digits.  Per pass: (1) per-tile digit histograms,
+// (2) one exclusive scan over the digit-major histogram matrix gives every
+// (digit, tile) its output offset, (3) each tile ranks its keys stably with
+// warp match/ballot, reorders them in shared memory and writes each digit's
+// run contiguously.
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048
+constexpr int kRsWarps = kRsThreads / 32;
+
+__global__ void k_rs_hist(const u64 *__restrict__ keys, i64 n, int shift, int ntiles,
+                          int *__restrict__ hist) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    i64 base = (i64)blockIdx.x * kRsTile;
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+        i64 i = base + (i64)k * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 255)], 1);
+    }
+    __syncthreads();
+    hist[(i64)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__restrict__ kout,
+             int *__restrict__ vout, i64 n, int shift, int ntiles, const int *__restrict__ offs) {
+    __shared__ u64 sk[kRsTile];
+    __shared__ int sv[kRsTile];
+    __shared__ int wcnt[kRsWarps][256];
+    __shared__ int dstart[256];
+    __shared__ int gofs[256];
+    __shared__ int total;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const i64 tile0 = (i64)blockIdx.x * kRsTile;
+    const int count = (int)min((i64)kRsTile, n - tile0);
+
+#pragma unroll
+    for (int k = 0; k < 256 / 32; ++k) wcnt[wid][k * 32 + lane] = 0;
+    __syncwarp();
+
+    u64 key[kRsItems];
+    int val[kRsItems], dig[kRsItems], rank[kRsItems];
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        int li = wid * (kRsItems * 32) + j * 32 + lane;
+        i64 i = tile0 + li;
+        bool ok = li < count;
+        key[j] = ok ? kin[i] : ~0ULL;
+        val[j] = ok ? vin[i] : 0;
+        dig[j] = ok ? (int)((key[j] >> shift) & 255) : 255;
+    }
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+        int before = __popc(peers & lt_mask);
+        int base = wcnt[wid][dig[j]];
+        __syncwarp();
+        if (before == 0) wcnt[wid][dig[j]] = base + __popc(peers);
+        __syncwarp();
+        rank[j] = base + before;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // 256 threads == 256 digits
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) {
+            int c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+        int ex = block_excl_scan<int, kRsThreads>(run, &total);
+        dstart[d] = ex;
+        gofs[d] = offs[(i64)d * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        int pos = dstart[dig[j]] + wcnt[wid][dig[j]] + rank[j];
+        sk[pos] = key[j];
+        sv[pos] = val[j];
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < count; p += kRsThreads) {
+        u64 k = sk[p];
+        int d = (int)((k >> shift) & 255);
+        i64 o = (i64)gofs[d] + (p - dstart[d]);
+        kout[o] = k;
+        vout[o] = sv[p];
+    }
+}
+
+size_t radix_tmp_words(i64 n) { return (size_t)256 * div_up(n > 0 ? n : 1, kRsTile) + 64; }
+
+int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int bits, u32 *tmp,
+                     int *scan_tmp, bool *in_b, cudaStream_t s) {
+    *in_b = false;
+    if (n <= 1 || bits <= 0) return MC_OK;
+    const int ntiles = div_up(n, kRsTile);
+    int *hist = reinterpret_cast<int *>(tmp);
+    u64 *ki = keysA, *ko = keysB;
+    int *vi = valsA, *vo = valsB;
+    for (int shift = 0; shift < bits; shift += 8) {
+        ++::mc::g_launches; k_rs_hist<<<ntiles, kRsThreads, 0, s>>>(ki, n, shift, ntiles, hist);
+        MC_TRY(exclusive_scan_i32(hist, hist, (i64)256 * ntiles, nullptr, scan_tmp, s));
+        ++::mc::g_launches; k_rs_scatter<<<ntiles, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, hist);
+        MC_CUDA(cudaGetLastError());
+        u64 *tk = ki; ki = ko; ko = tk;
+        int *tv = vi; vi = vo; vo = tv;
+        *in_b = !*in_b;
+    }
+    return MC_OK;
+}
+
+}  // namespace mc

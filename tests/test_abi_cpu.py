@@ -1,0 +1,61 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, and exports every entry point declared in include/*.h."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(mc_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1808_05458_gb300 import build
+    build.build_library()
+    from paper_1808_05458_gb300 import mincut
+    return mincut.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("mc_graph_create", "mc_min_cut", "mc_batch_min_cut", "mc_graph_destroy",
+              "mc_strerror"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for f in declared_functions():
+        assert hasattr(lib, f), f"{f} declared in include/ but not exported"
+
+
+def test_binding_covers_exports():
+    from paper_1808_05458_gb300 import mincut
+    assert set(declared_functions()) <= set(mincut.EXPORTS)
+
+
+def test_strerror_and_defaults_without_gpu(lib):
+    from paper_1808_05458_gb300 import mincut
+    assert "invalid" in mincut.strerror(mincut.MC_EINVAL)
+    o = mincut.options()
+    assert o.pr_level == 2 and o.pq_order == mincut.MC_PQ_LIFO
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    # n < 2 and NULL outputs are rejected before any CUDA call
+    h = ctypes.c_void_p()
+    import numpy as np
+    rp = np.zeros(2, dtype=np.int32)
+    assert lib.mc_graph_create(1, rp.ctypes.data, None, None, 0, ctypes.byref(h)) == -1
+    assert lib.mc_min_cut(None, None, None, None, None) == -1
+    assert lib.mc_graph_destroy(None) == -1

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work is compared bit-exact: canonical CSR, degrees, contraction,
+Padberg-Rinaldi blocks, and lambda.  A minimum cut's side is not unique, so
+the side is checked for validity: proper, canonical polarity, and its
+recomputed weight equals lambda.  Concurrent CAPFOREST unions are racy by
+design (Sec. 3.2), so a round of them is checked by what the paper's Lemma 2
+guarantees: contracting its blocks keeps min(lambda-hat, lambda(G/U)) =
+lambda(G).
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1808_05458_gb300 as m
+    m.load_library()
+    return m
+
+
+def check_cut(mc, g, res, lam_ref):
+    n = len(g[0]) - 1
+    side = res.side(n)
+    assert res.lam == lam_ref
+    assert side[0] == 0
+    if lam_ref > 0 or n > 1:
+        assert 0 < side.sum() < n
+    assert oracle.cut_weight(*g, side) == lam_ref
+
+
+def _random_tiny(rng, i):
+    n = int(rng.integers(2, 15))
+    kind = i % 4
+    if kind == 0:
+        g = graphgen.random_gnp(n, float(rng.uniform(0.2, 0.9)), seed=i, wmax=100)
+    elif kind == 1:
+        g = graphgen.random_gnp(n, float(rng.uniform(0.4, 1.0)), seed=i, wmax=3)
+    elif kind == 2:
+        g = graphgen.random_connected(n, int(rng.integers(0, 3 * n)), seed=i, wmax=10)
+    else:
+        m = int(rng.integers(1, 3 * n))
+        g = graphgen.from_edges(n, rng.integers(0, n, size=m), rng.integers(0, n, size=m),
+                                rng.integers(0, 6, size=m))
+    return n, g
+
+
+# ------------------------------------------------------------------ steps --
+def test_canonical_export_and_degrees(mc):
+    rng = np.random.default_rng(1)
+    for i in range(40):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        with mc.Graph(*g) as G:
+            rp, col, w = G.export()
+            orp, ocol, ow = oracle.contract(*g, np.arange(n, dtype=np.int32), n)
+            assert (rp == orp).all() and (col == ocol).all() and (w == ow).all()
+            assert (G.degrees() == oracle.degrees(*g)).all()
+
+
+def test_contract_parity_random_labels(mc):
+    rng = np.random.default_rng(2)
+    for i in range(30):
+        g = graphgen.random_connected(int(rng.integers(20, 3000)), int(rng.integers(0, 20000)),
+                                      seed=i, wmax=50)
+        n = len(g[0]) - 1
+        nc = int(rng.integers(1, n + 1))
+        lab = rng.integers(0, nc, size=n).astype(np.int32)
+        lab[rng.permutation(n)[:nc]] = np.arange(nc)
+        with mc.Graph(*g) as G:
+            rp, col, w = G.contract(lab, nc)
+        orp, ocol, ow = oracle.contract(*g, lab, nc)
+        assert (rp == orp).all() and (col == ocol).all() and (w == ow).all()
+
+
+def test_contract_clamp(mc):
+    g = graphgen.random_connected(500, 4000, seed=5, wmax=50)
+    n = len(g[0]) - 1
+    lab = (np.arange(n) // 7).astype(np.int32)
+    nc = int(lab.max()) + 1
+    with mc.Graph(*g) as G:
+        rp, col, w = G.contract(lab, nc, clamp=60)
+    orp, ocol, ow = oracle.contract(*g, lab, nc)
+    assert (rp == orp).all() and (col == ocol).all()
+    assert (w == np.minimum(ow, 60)).all()
+
+
+@pytest.mark.parametrize("level", [1, 2, 3, 4])
+def test_pr_parity(mc, level):
+    rng = np.random.default_rng(10 + level)
+    for i in range(25):
+        g = graphgen.random_connected(int(rng.integers(5, 400)), int(rng.integers(0, 2000)),
+                                      seed=100 * level + i, wmax=int(rng.integers(1, 30)))
+        deg = oracle.degrees(*g)
+        lam = int(deg.min()) - int(rng.integers(0, 3))
+        with mc.Graph(*g) as G:
+            lab = G.pr_tests(lam, level)
+        assert (lab == oracle.pr_tests(*g, lam, level)).all()
+
+
+def test_capforest_round_is_safe(mc):
+    # Lemma 2: every union of a concurrent capped round keeps the minimum cut
+    rng = np.random.default_rng(3)
+    for i in range(150):
+        n, g = _random_tiny(rng, i)
+        if n < 3:
+            continue
+        lam_g = oracle.brute_force(*g)[0]
+        deg = oracle.degrees(*g)
+        for budget in (0, 6):
+            with mc.Graph(*g) as G:
+                lab, lam_out, unions = G.capforest_round(int(deg.min()),
+                                                         mc.options(region_budget=budget, seed=i))
+            assert lam_out >= lam_g
+            roots, lab2 = np.unique(lab, return_inverse=True)
+            if len(roots) == 1:
+                assert lam_out == lam_g
+                continue
+            crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+            lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0] \
+                if len(roots) >= 2 else lam_out
+            assert min(lam_out, lam_c) == lam_g, (i, lam_out, lam_c, lam_g)
+
+
+def test_capforest_round_medium_safe(mc):
+    for i in range(6):
+        g = graphgen.planted(40 + i, block_n=150, avg_deg=10, cross=3)
+        lam_g = oracle.stoer_wagner(*g)[0]
+        deg = oracle.degrees(*g)
+        with mc.Graph(*g) as G:
+            lab, lam_out, unions = G.capforest_round(int(deg.min()))
+        assert unions > 0
+        roots, lab2 = np.unique(lab, return_inverse=True)
+        crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+        lam_c = oracle.stoer_wagner(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
+        assert min(lam_out, lam_c) == lam_g
+
+
+# ------------------------------------------------------------ full solves --
+def test_random_tiny_min_cut(mc):
+    rng = np.random.default_rng(4)
+    for i in range(400):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        ref = oracle.brute_force(*g)[0]
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(seed=i, pq_order=i % 2, pr_level=i % 5))
+        check_cut(mc, g, res, ref)
+
+
+@pytest.mark.parametrize("n,wt", [(2, 1), (3, 4), (10, 1), (33, 3), (100, 1)])
+def test_closed_form_complete(mc, n, wt):
+    g = graphgen.complete(n, wt)
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, (n - 1) * wt)
+
+
+@pytest.mark.parametrize("n,wt", [(3, 1), (50, 7), (5000, 2)])
+def test_closed_form_cycle(mc, n, wt):
+    g = graphgen.cycle(n, wt)
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, 2 * wt)
+
+
+def test_closed_form_two_cliques(mc):
+    for a, k in [(10, 3), (40, 7), (200, 11)]:
+        g = graphgen.two_cliques(a, k, seed=a)
+        with mc.Graph(*g) as G:
+            res = G.min_cut()
+        check_cut(mc, g, res, k)
+
+
+def test_disconnected_graph(mc):
+    g = graphgen.from_edges(7, np.array([0, 1, 3, 4, 5]), np.array([1, 2, 4, 5, 6]),
+                            np.array([3, 4, 5, 6, 7]))
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    side = res.side(7)
+    assert res.lam == 0 and oracle.cut_weight(*g, side) == 0 and side[0] == 0 and side.sum() == 4
+
+
+def test_tree_and_path(mc):
+    for seed in range(5):
+        g = graphgen.random_tree(3000, seed)
+        with mc.Graph(*g) as G:
+            res = G.min_cut()
+        check_cut(mc, g, res, int(g[2].min()))
+
+
+def test_medium_random_vs_stoer_wagner(mc):
+    for i in range(10):
+        g = graphgen.random_connected(200 + 150 * i, 600 + 900 * i, seed=1000 + i,
+                                      wmax=[1, 5, 100][i % 3])
+        ref = oracle.stoer_wagner(*g)[0]
+        for seed in range(2):
+            with mc.Graph(*g) as G:
+                res = G.min_cut(mc.options(seed=seed, pq_order=seed))
+            check_cut(mc, g, res, ref)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_planted_4096(mc, seed):
+    # the small plain-method workload, all ten seeds
+    g = graphgen.planted(seed)
+    ref, _, _ = oracle.noi(*g)
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, ref)
+
+
+def test_options_do_not_change_lambda(mc):
+    g = graphgen.rhg(5, 1 << 14, 24.0)
+    ref, _, _ = oracle.noi(*g)
+    for o in [dict(), dict(pq_order=1), dict(pr_level=0), dict(pr_level=4),
+              dict(region_budget=64), dict(region_budget=1500), dict(scans_per_round=64),
+              dict(seed=99)]:
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(**o))
+        check_cut(mc, g, res, ref)
+
+
+def test_device_pointer_graph(mc):
+    import torch
+    g = graphgen.planted(3, block_n=300, avg_deg=12, cross=4)
+    ref, _, _ = oracle.noi(*g)
+    t = [torch.from_numpy(a.copy()).cuda() for a in g]
+    with mc.Graph(*t) as G:
+        res = G.min_cut()
+    assert res.lam == ref
+    side = res.side(len(g[0]) - 1)
+    assert oracle.cut_weight(*g, side) == ref
+
+
+def test_input_conventions(mc):
+    # parallel arcs summed, self-loops and zero weights dropped
+    g = graphgen.from_edges(4, np.array([0, 0, 1, 2, 3, 1, 2]), np.array([1, 1, 2, 3, 3, 3, 0]),
+                            np.array([2, 3, 4, 5, 50, 0, 1]))
+    ref = oracle.brute_force(*g)[0]
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, ref)
+
+
+def test_invalid_inputs(mc):
+    rp = np.array([0, 1, 1], dtype=np.int32)  # arc 0->1 without its mirror
+    with pytest.raises(mc.MinCutError) as e:
+        mc.Graph(rp, np.array([1], dtype=np.int32), np.array([1], dtype=np.int32))
+    assert e.value.code == -1
+    rp, col, w = graphgen.cycle(5)
+    bad = col.copy()
+    bad[0] = 9
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(rp, bad, w)
+    neg = w.copy()
+    neg[:] = -1
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(rp, col, neg)
+    badrp = rp.copy()
+    badrp[2] = 0
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(badrp, col, w)
+
+
+def test_batch_small(mc):
+    b = graphgen.batch(7, G=48)
+    lam, _, _, _ = mc.batch_min_cut(*b)
+    for k in range(48):
+        g = graphgen.batch_graph(b, k)
+        assert lam[k] == oracle.noi(*g)[0], k
+
+
+# ------------------------------------------------------------ full sizes --
+def test_rhg_2_20_full_size(mc):
+    # the plain-path workload: RHG n = 2^20, average degree 32, exponent 5
+    g = graphgen.rhg(1, 1 << 20, 32.0, 5.0)
+    ref, _, _ = oracle.noi(*g)
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, ref)
+
+
+def test_rmat_kcore_scale20(mc):
+    g = graphgen.rmat_kcore(1, scale=20)
+    ref, _, _ = oracle.noi(*g)
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, ref)
