@@ -64,7 +64,8 @@ typedef struct mc_options {
     int32_t pq_order;        /* MC_PQ_LIFO (default) or MC_PQ_FIFO             */
     int32_t bound;           /* MC_BOUND_DEGREE (default) or MC_BOUND_LP       */
     int32_t pr_level;        /* Padberg-Rinaldi tests 1..pr_level, 0 = off;
-                                default 2                                       */
+                                PR1/PR2 run every round, PR3/PR4 in rounds whose
+                                scans unite < n/4 vertices; default 4           */
     int32_t scans_per_round; /* concurrent CAPFOREST warps, 0 = auto           */
     int32_t region_budget;   /* max vertices touched by one scan, 0 = auto     */
     int32_t lp_iters;        /* label-propagation sweeps for MC_BOUND_LP, 0=auto*/
@@ -191,6 +192,14 @@ int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels);
  * after the scans' alpha updates, *unions_out = successful unions.         */
 int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt,
                       int32_t *labels, int64_t *lam_out, int64_t *unions_out);
+
+/* One full CAPFOREST scan (Alg. 3) of the whole graph from vertex `start`
+ * at bound `lam`, queue capped at lam (Lemma 1): labels[v] = smallest vertex
+ * of v's block after uniting every edge whose certificate crosses lam,
+ * *lam_out = the bound after the scan's alpha updates, *unions_out = unions.
+ * Deterministic for given inputs.                                        */
+int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *labels,
+                           int64_t *lam_out, int64_t *unions_out);
 
 /* `iters` label-propagation sweeps (reading stated in DESIGN and in the
  * kernel source); labels n int32.                                         */

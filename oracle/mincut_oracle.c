@@ -656,7 +656,13 @@ int orc_label_prop(int n, const int32_t *rp, const int32_t *col,
 /*   PR4: c(u,v) + sum over common neighbours w of min(c(u,w), c(v,w)) >= lam   */
 /* PR2 and PR3 are strict because every edge that passes is contracted at      */
 /* once: with ">=" a path of weight-w edges through degree-2w vertices would   */
-/* be contracted whole and its cut of weight w lost.  `level` selects the      */
+/* be contracted whole and its cut of weight w lost.  With level >= 2 one more */
+/* rule covers the tie PR2 leaves out: a vertex u with exactly two neighbours  */
+/* joined by equal weights c is united with the smaller of the two.  Any cut   */
+/* below delta = min degree <= 2c crosses a maximal path of such vertices at   */
+/* most once, can be slid along it without changing its weight, and the path's */
+/* k inner vertices unite at most k of its k+1 edges, so one stays open;      */
+/* a graph that is one such cycle has lambda = delta.  `level` selects the     */
 /* tests 1..level.  labels[v] receives the smallest vertex of v's block in the  */
 /* graph of all passing edges.                                                 */
 int orc_pr_tests(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
@@ -698,6 +704,13 @@ int orc_pr_tests(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
             if (ok) uf_union(par, u, v);
         }
         for (a = g.rp[u]; a < g.rp[u + 1]; ++a) cw[g.col[a]] = 0;
+    }
+    if (level >= 2) {
+        for (u = 0; u < n; ++u) {
+            a = g.rp[u];
+            if (g.rp[u + 1] - a == 2 && g.w[a] == g.w[a + 1])
+                uf_union(par, u, g.col[a] < g.col[a + 1] ? g.col[a] : g.col[a + 1]);
+        }
     }
     for (v = 0; v < n; ++v) labels[v] = uf_find(par, v);
     free(deg); free(cw); free(par);

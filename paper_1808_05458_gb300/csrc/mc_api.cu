@@ -8,6 +8,7 @@
 // original vertices (Sec. 3.3): a scan's prefix for an alpha cut, the
 // preimage of a contracted vertex for a degree cut.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -197,40 +198,68 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
     int rounds = 0, fallbacks = 0, guard = 0;
+    const bool verbose = getenv("MC_VERBOSE") != nullptr;
     while (cur.n >= 2 && lam > 0) {
         if (++guard > 4 * n0 + 64) return MC_EINTERNAL;
         cfg.round = rounds + guard;
         MC_TRY(union_find_init(w.par, cur.n, s));
         MC_TRY(round_reset(w, lam, s));
         if (o.pr_level > 0) {
-            MC_TRY(pr_tests(cur, w, lam, o.pr_level, s));
+            MC_TRY(pr_tests_budget(cur, w, lam, 1, o.pr_level < 2 ? o.pr_level : 2, 64, s));
             bytes += cur.arcs * 16;
         }
         S.ms_pr += ph.ms();
-        MC_CUDA(cudaEventRecord(ka, s));
-        MC_TRY(capforest_parallel(cur, w, cfg, s));
-        MC_CUDA(cudaEventRecord(kb, s));
-        MC_TRY(status_read(w, s));
-        {
+        // concurrent capped scans; returns the round's cumulative unions and
+        // records a side if some scan's alpha lowered lambda-hat
+        auto scan_round = [&](int budget, i64 *unions_out) -> int {
+            ScanConfig c2 = cfg;
+            c2.budget = budget;
+            MC_CUDA(cudaEventRecord(ka, s));
+            MC_TRY(capforest_parallel(cur, w, c2, s));
+            MC_CUDA(cudaEventRecord(kb, s));
+            MC_TRY(status_read(w, s));
             float t = 0;
             cudaEventElapsedTime(&t, ka, kb);
             S.ms_scan_kernel += t;
             S.scan_launches += 1;
+            const Status st = *w.h_st;
+            S.scanned_arcs += st.scanned_arcs;
+            S.scanned_verts += st.scanned_verts;
+            if (verbose)
+                fprintf(stderr, "[mc] round %d n=%d arcs=%lld lam=%lld budget=%d unions=%lld scans=%lld "
+                        "scanned_v=%lld scanned_a=%lld black=%lld lam_after=%lld (%.3f ms)\n", rounds,
+                        cur.n, (long long)cur.arcs, (long long)lam, budget, (long long)st.unions,
+                        (long long)st.scans, (long long)st.scanned_verts, (long long)st.scanned_arcs,
+                        (long long)st.blacklisted, (long long)st.lam, t);
+            bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
+            if (st.lam < lam && st.best_scan > 0) {
+                MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
+                lam = st.lam;
+            }
+            *unions_out = st.unions;
+            return MC_OK;
+        };
+        i64 unions = 0;
+        MC_TRY(scan_round(cfg.budget, &unions));
+        S.ms_capforest += ph.ms();
+        // a poor round: the triangle tests PR3/PR4 add their unions
+        if (o.pr_level >= 3 && unions * 4 < cur.n) {
+            MC_TRY(pr_tests_budget(cur, w, lam, 3, o.pr_level, 64, s));
+            MC_TRY(status_read(w, s));
+            unions = w.h_st->unions;
+            bytes += cur.arcs * 16;
+            S.ms_pr += ph.ms();
         }
-        Status st = *w.h_st;
-        S.scanned_arcs += st.scanned_arcs;
-        S.scanned_verts += st.scanned_verts;
-        bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
-        if (st.lam < lam && st.best_scan > 0) {
-            MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
-            lam = st.lam;
+        // nothing united: wide scans first, then one full scan (Alg. 2)
+        if (unions == 0) {
+            MC_TRY(scan_round(1536, &unions));
+            S.ms_capforest += ph.ms();
         }
-        i64 unions = st.unions;
         if (unions == 0) {
             const i64 lam_before = lam;
             MC_TRY(capforest_full(cur, w, cfg, s));
             MC_TRY(status_read(w, s));
-            st = *w.h_st;
+            const Status st = *w.h_st;
             S.scanned_arcs += st.scanned_arcs;
             S.scanned_verts += st.scanned_verts;
             bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
@@ -240,6 +269,9 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             }
             unions = st.unions;
             ++fallbacks;
+            if (verbose)
+                fprintf(stderr, "[mc] round %d full scan: unions=%lld lam=%lld\n", rounds,
+                        (long long)unions, (long long)lam);
             if (unions == 0) {
                 S.ms_capforest += ph.ms();
                 if (lam < lam_before) continue;  // lambda-hat dropped inside the scan: rescan
@@ -258,7 +290,13 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             lam = w.h_st->mindeg;
             MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
         }
-        S.ms_contract += ph.ms();
+        {
+            double t = ph.ms();
+            S.ms_contract += t;
+            if (verbose)
+                fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld (%.3f ms) lam=%lld\n", nxt->n,
+                        (long long)nxt->arcs, t, (long long)lam);
+        }
         cur = *nxt;
         nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
         ++rounds;
@@ -282,7 +320,7 @@ int mc_options_default(mc_options *opt) {
     memset(opt, 0, sizeof(*opt));
     opt->pq_order = MC_PQ_LIFO;
     opt->bound = MC_BOUND_DEGREE;
-    opt->pr_level = 2;
+    opt->pr_level = 4;
     opt->scans_per_round = 0;
     opt->region_budget = 0;
     opt->lp_iters = 0;
@@ -435,7 +473,7 @@ int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels) {
     cudaStream_t s = g->stream;
     MC_TRY(union_find_init(g->w.par, g->n0, s));
     MC_TRY(round_reset(g->w, lam, s));
-    MC_TRY(pr_tests_budget(g->G0, g->w, lam, level, -1, s));
+    MC_TRY(pr_tests_budget(g->G0, g->w, lam, 1, level, -1, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
@@ -456,6 +494,24 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     MC_TRY(union_find_init(g->w.par, g->n0, s));
     MC_TRY(round_reset(g->w, lam, s));
     MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));
+    MC_TRY(flatten_labels(g->w, g->n0, s));
+    MC_TRY(status_read(g->w, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (lam_out) *lam_out = g->w.h_st->lam;
+    if (unions_out) *unions_out = g->w.h_st->unions;
+    return MC_OK;
+}
+
+int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *labels, int64_t *lam_out,
+                           int64_t *unions_out) {
+    if (!g || !labels || start < 0 || start >= g->n0) return MC_EINVAL;
+    cudaStream_t s = g->stream;
+    ScanConfig cfg;
+    cfg.start = start;
+    MC_TRY(union_find_init(g->w.par, g->n0, s));
+    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(capforest_full(g->G0, g->w, cfg, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_TRY(status_read(g->w, s));
     MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));

@@ -23,10 +23,12 @@
 //   r(y) += c; key(y) = min(r(y), C)  (never lowered)
 // Each scanned x updates alpha += c(x) - 2 r(x) = c(S), the cut between the
 // scanned set S and the rest, and lowers lambda-hat while S != V (Alg. 1).
-// A scan ends when its queue is empty or its table reaches its budget; early
-// termination keeps every union valid (Lemma 2 part 2).  If a table cannot
-// take a neighbour, that arc is left unscanned -- Lemma 1's argument with the
-// arc's weight lowered to 0 -- and the scan stops reporting alpha.
+// A scan ends when its queue is empty.  Once its table holds `budget`
+// vertices it takes no new ones: an arc to a vertex it cannot hold is left
+// unscanned -- Lemma 1's argument with that arc's weight lowered to 0, the
+// refused vertex never entering the scan -- so the scan goes on over the
+// vertices it holds and stops reporting alpha.  Ending a scan early keeps
+// every union valid (Lemma 2 part 2).
 #include <cstdio>
 
 #include "mc_internal.cuh"
@@ -165,6 +167,7 @@ struct ScanSmem {
 
 template <int HC>
 struct LogHC;
+template <> struct LogHC<256> { static constexpr int v = 8; };
 template <> struct LogHC<512> { static constexpr int v = 9; };
 template <> struct LogHC<1024> { static constexpr int v = 10; };
 template <> struct LogHC<2048> { static constexpr int v = 11; };
@@ -303,10 +306,10 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
                 c = e.y;
             }
             int s2 = v ? tab.find(y) : -1;
-            if (__any_sync(0xffffffffu, v && s2 < 0)) {
-                alpha_ok = false;
-                stop = true;
-            }
+            // a full table refuses new vertices: the arc stays unscanned (its
+            // weight is 0 in Lemma 1's lowered graph) and alpha is no longer
+            // the cut of S, but the scan goes on over the vertices it holds
+            if (__any_sync(0xffffffffu, v && s2 < 0)) alpha_ok = false;
             bool push = false;
             int kn = 0;
             if (s2 >= 0) {
@@ -542,10 +545,13 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
     MC_CUDA(cudaMemsetAsync(w.T, 0, sizeof(int) * (size_t)g.n, s));
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
-    int budget = cfg.budget > 0 ? cfg.budget : 768;
+    int budget = cfg.budget > 0 ? cfg.budget : 192;
     constexpr int WPB = 4;
     int rc;
-    if (budget <= 384 - 32) {
+    if (budget <= 192) {
+        A.limit = budget;
+        rc = launch_parallel<WPB, 256, 256>(A, cfg.pq_fifo, cfg.warps, s);
+    } else if (budget <= 384 - 32) {
         A.limit = budget;
         rc = launch_parallel<WPB, 512, 256>(A, cfg.pq_fifo, cfg.warps, s);
     } else if (budget <= 768) {
@@ -567,7 +573,7 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
     MC_CUDA(cudaMemsetAsync(w.fb_r, 0, sizeof(int) * (size_t)g.n, s));
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
-    const int start = (int)(A.perm_b % (u64)(g.n > 0 ? g.n : 1));
+    const int start = cfg.start >= 0 && cfg.start < g.n ? cfg.start : (int)(A.perm_b % (u64)(g.n > 0 ? g.n : 1));
     const i64 pool = g.arcs + 2;
     int *eslot = reinterpret_cast<int *>(w.fb_pool);
     int *enext = eslot + pool;

@@ -179,6 +179,7 @@ struct ScanConfig {
     int budget = 0;        // touched-vertex budget per scan (0 = auto)
     u64 seed = 0;
     int round = 0;
+    int start = -1;        // full scan start vertex (-1 = from seed and round)
 };
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
 // one full CAPFOREST scan (Alg. 3) from a start vertex, single warp
@@ -190,7 +191,10 @@ int side_from_scan(Work &w, int n0, int scan, int len, cudaStream_t s);
 int side_from_component(Work &w, int n0, cudaStream_t s);  // par = CC roots
 int orig_update(Work &w, int n0, cudaStream_t s);           // orig = lab[orig]
 
-int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int level, int budget, cudaStream_t s);
+// tests lo..level; PR3/PR4 only on edges whose shorter row has <= budget arcs
+// (every edge if budget < 0)
+int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int budget,
+                    cudaStream_t s);
 int flatten_labels(Work &w, int n, cudaStream_t s);   // par[v] = root, labels in par
 int round_reset(Work &w, i64 lam, cudaStream_t s);    // st->lam = lam, counters = 0
 int side_canon(Work &w, int n0, cudaStream_t s);

@@ -13,6 +13,10 @@
 // delta that separates u and v could be made strictly lighter by moving u
 // or v across, so no minimum cut below lambda-hat crosses the edge; the
 // strict inequality is what lets all passing edges be contracted at once.
+// With level >= 2 a vertex with exactly two neighbours joined by equal
+// weights also joins the smaller neighbour: a cut below delta crosses a path
+// of such vertices at most once and slides along it at equal weight, and a
+// path's k inner vertices close at most k of its k+1 edges.
 //
 // One thread per arc (u < v).  PR3/PR4 walk the shorter of the two sorted
 // rows and binary-search each neighbour in the longer one, only when the
@@ -32,7 +36,7 @@ __device__ __forceinline__ int row_weight(const int *rp, const int2 *adj, int v,
     return 0;
 }
 
-__global__ void k_pr(const DevGraph g, int *par, long long lam, int level, int budget,
+__global__ void k_pr(const DevGraph g, int *par, long long lam, int lo, int level, int budget,
                      unsigned long long *unions) {
     long long local = 0;
     for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
@@ -42,7 +46,8 @@ __global__ void k_pr(const DevGraph g, int *par, long long lam, int level, int b
         if (u >= v) continue;
         const long long c = e.y;
         const long long du = g.deg[u], dv = g.deg[v];
-        bool ok = (level >= 1 && c >= lam) || (level >= 2 && 2 * c > (du < dv ? du : dv));
+        bool ok = (lo <= 1 && level >= 1 && c >= lam) ||
+                  (lo <= 2 && level >= 2 && 2 * c > (du < dv ? du : dv));
         if (!ok && level >= 3) {
             const int lu = g.rp[u + 1] - g.rp[u], lv = g.rp[v + 1] - g.rp[v];
             const int a = lu <= lv ? u : v, b = lu <= lv ? v : u;
@@ -59,28 +64,40 @@ __global__ void k_pr(const DevGraph g, int *par, long long lam, int level, int b
                     const long long cvw = (a == u) ? cb : x.y;
                     if (2 * (c + cuw) > du && 2 * (c + cvw) > dv) ok = true;
                     pr4 += cuw < cvw ? cuw : cvw;
+                    if (level >= 4 && pr4 >= lam) ok = true;  // early exit
                 }
                 if (!ok && level >= 4 && pr4 >= lam) ok = true;
             }
         }
         if (ok && uf_union(par, u, v)) ++local;
     }
+    // degree-2 tie rule: a vertex with exactly two neighbours of equal weight
+    // joins the smaller one (a cut below delta slides along such a path)
+    if (lo <= 2 && level >= 2) {
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.n; u += gridDim.x * blockDim.x) {
+            const int a = g.rp[u];
+            if (g.rp[u + 1] - a != 2) continue;
+            const int2 e0 = g.adj[a], e1 = g.adj[a + 1];
+            if (e0.y == e1.y && uf_union(par, u, e0.x < e1.x ? e0.x : e1.x)) ++local;
+        }
+    }
     if (local) atomicAdd(unions, (unsigned long long)local);
 }
 
-int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int level, int budget, cudaStream_t s) {
-    if (level <= 0 || g.arcs == 0) return MC_OK;
-    int blocks = (int)((g.arcs + 255) / 256);
+int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int budget,
+                    cudaStream_t s) {
+    if (level <= 0 || lo > level || g.arcs == 0) return MC_OK;
+    int blocks = (int)(((g.arcs > g.n ? g.arcs : g.n) + 255) / 256);
     int cap = num_sms() * 16;
     if (blocks > cap) blocks = cap;
-    ++::mc::g_launches; k_pr<<<blocks, 256, 0, s>>>(g, w.par, lam, level, budget,
+    ++::mc::g_launches; k_pr<<<blocks, 256, 0, s>>>(g, w.par, lam, lo, level, budget,
                                 reinterpret_cast<unsigned long long *>(&w.st->unions));
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
 
 int pr_tests(const DevGraph &g, Work &w, i64 lam, int level, cudaStream_t s) {
-    return pr_tests_budget(g, w, lam, level, 64, s);
+    return pr_tests_budget(g, w, lam, 1, level, 64, s);
 }
 
 }  // namespace mc

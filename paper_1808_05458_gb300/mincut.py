@@ -63,7 +63,7 @@ _lib = None
 EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_graph_size",
            "mc_min_cut", "mc_batch_min_cut", "mc_strerror", "mc_graph_export",
            "mc_step_degrees", "mc_step_contract", "mc_step_pr", "mc_step_capforest",
-           "mc_step_label_prop")
+           "mc_step_capforest_full", "mc_step_label_prop")
 
 
 def library_path() -> str:
@@ -95,6 +95,7 @@ def load_library():
     lib.mc_step_contract.argtypes = [vp, vp, i32, i64, vp, vp, vp, P(i64)]
     lib.mc_step_pr.argtypes = [vp, i64, i32, vp]
     lib.mc_step_capforest.argtypes = [vp, i64, P(McOptions), vp, P(i64), P(i64)]
+    lib.mc_step_capforest_full.argtypes = [vp, i64, i32, vp, P(i64), P(i64)]
     lib.mc_step_label_prop.argtypes = [vp, i32, u64, vp]
     for f in EXPORTS:
         if f != "mc_strerror":
@@ -257,6 +258,15 @@ class Graph:
         _check(load_library().mc_step_capforest(self._h, lam, ctypes.byref(o), _ptr(lab),
                                                 ctypes.byref(lo), ctypes.byref(un)),
                "mc_step_capforest")
+        return lab, lo.value, un.value
+
+    def capforest_full(self, lam: int, start: int = 0):
+        """One full CAPFOREST scan (Alg. 3): (labels, lambda-hat after, unions)."""
+        lab = np.zeros(self.n, dtype=np.int32)
+        lo, un = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().mc_step_capforest_full(self._h, lam, start, _ptr(lab),
+                                                     ctypes.byref(lo), ctypes.byref(un)),
+               "mc_step_capforest_full")
         return lab, lo.value, un.value
 
     def label_prop(self, iters: int, seed: int) -> np.ndarray:

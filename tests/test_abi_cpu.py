@@ -48,7 +48,7 @@ def test_strerror_and_defaults_without_gpu(lib):
     from paper_1808_05458_gb300 import mincut
     assert "invalid" in mincut.strerror(mincut.MC_EINVAL)
     o = mincut.options()
-    assert o.pr_level == 2 and o.pq_order == mincut.MC_PQ_LIFO
+    assert o.pr_level == 4 and o.pq_order == mincut.MC_PQ_LIFO
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):

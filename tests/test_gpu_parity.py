@@ -139,6 +139,9 @@ def test_capforest_round_medium_safe(mc):
             lab, lam_out, unions = G.capforest_round(int(deg.min()))
         assert unions > 0
         roots, lab2 = np.unique(lab, return_inverse=True)
+        if len(roots) == 1:
+            assert lam_out == lam_g
+            continue
         crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
         lam_c = oracle.stoer_wagner(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
         assert min(lam_out, lam_c) == lam_g
@@ -296,3 +299,33 @@ def test_rmat_kcore_scale20(mc):
     with mc.Graph(*g) as G:
         res = G.min_cut()
     check_cut(mc, g, res, ref)
+
+
+def test_capforest_full_scan_safe_and_progresses(mc):
+    # Alg. 3: a full scan at lambda-hat <= delta unites at least one edge
+    # unless alpha lowered lambda-hat during the scan (Sec. 2.2), and every
+    # union keeps min(lambda-hat, lambda(G/U)) = lambda(G) (Lemma 1)
+    rng = np.random.default_rng(8)
+    for i in range(200):
+        n, g = _random_tiny(rng, i)
+        if n < 3:
+            continue
+        lam_g = oracle.brute_force(*g)[0]
+        deg = oracle.degrees(*g)
+        bound = int(deg.min())
+        if bound == 0:
+            continue
+        with mc.Graph(*g) as G:
+            lab, lam_out, unions = G.capforest_full(bound, start=i % n)
+            lab2_again, lam2, un2 = G.capforest_full(bound, start=i % n)
+        assert (lab == lab2_again).all() and lam_out == lam2 and unions == un2  # deterministic
+        assert lam_out >= lam_g
+        if lam_out == bound and lam_g > 0:
+            assert unions >= 1
+        roots, lab2 = np.unique(lab, return_inverse=True)
+        if len(roots) == 1:
+            assert lam_out == lam_g
+            continue
+        crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+        lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
+        assert min(lam_out, lam_c) == lam_g, (i, lam_out, lam_c, lam_g)

@@ -317,3 +317,70 @@ def test_planted_4096_two_exact_algorithms_agree():
     noi, s2, _ = oracle.noi(*g)
     assert sw == noi <= 8
     assert oracle.cut_weight(*g, s1) == sw and oracle.cut_weight(*g, s2) == sw
+
+
+def _subdivided(rng, i):
+    # a small random base graph whose edges are replaced by paths of equal
+    # weight (degree-2 chains), plus a few chords
+    nb = int(rng.integers(2, 6))
+    base = [(a, b) for a in range(nb) for b in range(a + 1, nb) if rng.random() < 0.7]
+    if not base:
+        base = [(0, 1)]
+    u, v, w = [], [], []
+    nxt = nb
+    for a, b in base:
+        k = int(rng.integers(0, 4))
+        c = int(rng.integers(1, 4))
+        chain = [a] + list(range(nxt, nxt + k)) + [b]
+        nxt += k
+        for x, y in zip(chain, chain[1:]):
+            u.append(x); v.append(y); w.append(c)
+    n = nxt
+    if n > 16:
+        return None
+    for _ in range(int(rng.integers(0, 3))):
+        x, y = rng.integers(0, n, size=2)
+        if x != y:
+            u.append(int(x)); v.append(int(y)); w.append(int(rng.integers(1, 4)))
+    return n, graphgen.from_edges(n, np.array(u), np.array(v), np.array(w))
+
+
+def test_pr_degree2_tie_rule_preserves_lambda():
+    # the degree-2 tie rule (level >= 2) on graphs full of equal-weight chains
+    rng = np.random.default_rng(21)
+    checked = 0
+    while checked < 400:
+        r = _subdivided(rng, checked)
+        if r is None:
+            continue
+        n, g = r
+        lam = oracle.brute_force(*g)[0]
+        bound = int(oracle.degrees(*g).min())
+        lab = oracle.pr_tests(*g, bound, 2)
+        roots, lab2 = np.unique(lab, return_inverse=True)
+        if len(roots) > 1:
+            crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+            lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
+        else:
+            lam_c = bound
+        assert min(bound, lam_c) == lam, (checked, bound, lam_c, lam)
+        checked += 1
+
+
+def test_pr_degree2_tie_rule_cycle_and_chain():
+    # a unit cycle collapses in one application (lambda = delta = 2) ...
+    g = graphgen.cycle(12)
+    assert len(np.unique(oracle.pr_tests(*g, 2, 2))) == 1
+    # ... and a unit chain between two cliques keeps one chain edge open
+    a = 8
+    iu, ju = np.triu_indices(a, 1)
+    k = 5
+    chain = [0] + list(range(2 * a, 2 * a + k)) + [a]
+    u = np.concatenate([iu, iu + a, chain[:-1]])
+    v = np.concatenate([ju, ju + a, chain[1:]])
+    g = graphgen.from_edges(2 * a + k, u, v)
+    lab = oracle.pr_tests(*g, 2, 2)
+    assert lab[0] != lab[a]
+    roots, lab2 = np.unique(lab, return_inverse=True)
+    crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+    assert oracle.stoer_wagner(crp.astype(np.int32), ccol, cw.astype(np.int32))[0] == 1
