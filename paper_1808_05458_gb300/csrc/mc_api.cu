@@ -475,7 +475,7 @@ int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels) {
     MC_TRY(round_reset(g->w, lam, s));
     MC_TRY(pr_tests_budget(g->G0, g->w, lam, 1, level, -1, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
-    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.root, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
     return MC_OK;
 }
@@ -496,7 +496,7 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_TRY(status_read(g->w, s));
-    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.root, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
     if (lam_out) *lam_out = g->w.h_st->lam;
     if (unions_out) *unions_out = g->w.h_st->unions;
@@ -514,7 +514,7 @@ int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *lab
     MC_TRY(capforest_full(g->G0, g->w, cfg, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_TRY(status_read(g->w, s));
-    MC_CUDA(cudaMemcpyAsync(labels, g->w.par, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.root, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
     if (lam_out) *lam_out = g->w.h_st->lam;
     if (unions_out) *unions_out = g->w.h_st->unions;

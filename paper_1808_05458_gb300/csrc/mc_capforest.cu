@@ -64,7 +64,10 @@ struct BucketQ {
     }
 };
 
-// lanes with `want` push (slot s, key k); all lanes call.  false = no room
+// lanes with `want` push (slot s, key k); all lanes call.  false = no room.
+// Lanes pushing into the same bucket are chained in lane order (found with
+// match_any), so a push needs no atomics on list heads and the resulting
+// order -- hence the scan order among equal keys -- is deterministic.
 template <class Idx, int NB>
 __device__ bool pq_push(BucketQ<Idx, NB> &q, bool want, int s, int k) {
     const int lane = threadIdx.x & 31;
@@ -78,23 +81,35 @@ __device__ bool pq_push(BucketQ<Idx, NB> &q, bool want, int s, int k) {
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base < 0) return false;
-    int e = base + __popc(m & ((1u << lane) - 1u));
-    int b = want ? q.bucket(k) : 0;
-    if (want) {
-        q.eslot[e] = (Idx)s;
-        q.enext[e] = q.NIL;
-    }
+    const int e = base + __popc(m & ((1u << lane) - 1u));
+    const int b = want ? q.bucket(k) : -1 - lane;  // distinct dummies for idle lanes
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const unsigned below = peers & ((1u << lane) - 1u);
+    const unsigned above = peers & ~((2u << lane) - 1u);
+    const int lo_lane = below ? 31 - __clz(below) : lane;  // next lower peer
+    const int hi_lane = above ? __ffs(above) - 1 : lane;   // next higher peer
+    const int e_lo = __shfl_sync(0xffffffffu, e, lo_lane);
+    const int e_hi = __shfl_sync(0xffffffffu, e, hi_lane);
+    const bool first = want && !below, last = want && !above;
+    int old = -1;
+    if (first) old = q.fifo ? q.tail[b] : q.head[b];
     __syncwarp();
     if (want) {
+        q.eslot[e] = (Idx)s;
         if (!q.fifo) {
-            int old = atomicExch(&q.head[b], e);
-            q.enext[e] = (Idx)old;
+            // LIFO: the highest lane becomes the head, each lane points down
+            q.enext[e] = first ? (old < 0 ? q.NIL : (Idx)old) : (Idx)e_lo;
+            if (last) q.head[b] = e;
         } else {
-            int old = atomicExch(&q.tail[b], e);
-            if (old < 0) q.head[b] = e;
-            else q.enext[old] = (Idx)e;
+            // FIFO: append in lane order after the old tail
+            q.enext[e] = last ? q.NIL : (Idx)e_hi;
+            if (first) {
+                if (old < 0) q.head[b] = e;
+                else q.enext[old] = (Idx)e;
+            }
+            if (last) q.tail[b] = e;
         }
-        atomicOr(&q.bits[b >> 5], 1u << (b & 31));
+        if (first) atomicOr(&q.bits[b >> 5], 1u << (b & 31));
     }
     __syncwarp();
     return true;

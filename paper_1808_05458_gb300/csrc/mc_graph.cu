@@ -46,6 +46,7 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
     w.cap_arcs = arcs0;
     i64 a = arcs0 > n0 ? arcs0 : n0;
     MC_TRY(dev_alloc_n(&w.par, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.root, (size_t)n0, s));
     MC_TRY(dev_alloc_n(&w.lab, (size_t)n0, s));
     MC_TRY(dev_alloc_n(&w.T, (size_t)n0, s));
     MC_TRY(dev_alloc_n(&w.order, (size_t)n0, s));
@@ -68,7 +69,7 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
 }
 
 void work_free(Work &w, cudaStream_t s) {
-    void *ps[] = {w.par, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
+    void *ps[] = {w.par, w.root, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
                   w.valsA, w.valsB, w.radix_tmp, w.rec_alpha, w.rec_len, w.fb_r, w.fb_pool,
                   w.best_side, w.st};
     for (void *p : ps) dev_free(p, s);
@@ -87,19 +88,22 @@ int union_find_init(int *par, int n, cudaStream_t s) {
     return MC_OK;
 }
 
-// flatten: par[v] = root(v); cnt[v] = (v is a root)
-__global__ void k_flatten(int *par, int *cnt, int n) {
+// flatten: root[v] = root of v in par; cnt[v] = (v is a root).  The roots go
+// to their own array: a find's path-halving store into par[v] may land after
+// v's own root store and leave par[v] at a lower ancestor, so par is never
+// the output.
+__global__ void k_flatten(int *par, int *__restrict__ root, int *__restrict__ cnt, int n) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int r = uf_find(par, v);
         cnt[v] = (r == v);
-        par[v] = r;
+        root[v] = r;
     }
 }
 
 // lab[v] = lab[root(v)]; roots already hold their new id from the scan
-__global__ void k_relabel(const int *__restrict__ par, int *lab, int n) {
+__global__ void k_relabel(const int *__restrict__ root, int *lab, int n) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int r = par[v];
+        int r = root[v];
         if (r != v) lab[v] = lab[r];
     }
 }
@@ -334,11 +338,11 @@ int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool f
                    cudaStream_t s) {
     const int n = in.n;
     if (flatten) {
-        ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.cnt, n);
+        ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n);
         int *d_total = reinterpret_cast<int *>(&w.st->count);
         ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
         MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, d_total, w.scan_tmp, s));
-        ++::mc::g_launches; k_relabel<<<grid_for(n), kThreads, 0, s>>>(w.par, w.lab, n);
+        ++::mc::g_launches; k_relabel<<<grid_for(n), kThreads, 0, s>>>(w.root, w.lab, n);
         MC_TRY(status_read(w, s));
         nc = (int)w.h_st->count;
     }
@@ -413,7 +417,7 @@ __global__ void k_cc_union(const DevGraph g, int *par) {
 int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s) {
     MC_TRY(union_find_init(w.par, g.n, s));
     if (g.arcs > 0) { ++::mc::g_launches; k_cc_union<<<grid_for(g.arcs), kThreads, 0, s>>>(g, w.par); }
-    ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.cnt, g.n);
+    ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
     MC_TRY(exclusive_scan_i32(w.cnt, w.lab, g.n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
     MC_TRY(status_read(w, s));
@@ -449,8 +453,8 @@ struct SideScan {
     }
 };
 struct SideComp {
-    const int *par;
-    __device__ bool operator()(int v) const { return par[v] != par[0]; }
+    const int *root;
+    __device__ bool operator()(int v) const { return root[v] != root[0]; }
 };
 
 static int side_grid(int n0) { return grid_for(((i64)n0 + 31) / 32 * 32); }
@@ -468,7 +472,7 @@ int side_from_scan(Work &w, int n0, int scan, int len, cudaStream_t s) {
 }
 
 int side_from_component(Work &w, int n0, cudaStream_t s) {
-    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideComp{w.par});
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideComp{w.root});
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
@@ -489,7 +493,7 @@ int orig_update(Work &w, int n0, cudaStream_t s) {
 namespace mc {
 
 int flatten_labels(Work &w, int n, cudaStream_t s) {
-    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.cnt, n);
+    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }

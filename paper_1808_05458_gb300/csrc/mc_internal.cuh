@@ -116,6 +116,7 @@ int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int 
 struct Work {
     // per-vertex (sized n0)
     int *par = nullptr;      // union-find parents
+    int *root = nullptr;     // union-find roots after a flatten (labels)
     int *lab = nullptr;      // relabel map
     int *T = nullptr;        // scan owner of each vertex (0 = unvisited)
     int *order = nullptr;    // visit index inside the owning scan
@@ -195,7 +196,7 @@ int orig_update(Work &w, int n0, cudaStream_t s);           // orig = lab[orig]
 // (every edge if budget < 0)
 int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int budget,
                     cudaStream_t s);
-int flatten_labels(Work &w, int n, cudaStream_t s);   // par[v] = root, labels in par
+int flatten_labels(Work &w, int n, cudaStream_t s);   // w.root[v] = root of v in w.par
 int round_reset(Work &w, i64 lam, cudaStream_t s);    // st->lam = lam, counters = 0
 int side_canon(Work &w, int n0, cudaStream_t s);
 int iota_i32(int *a, int n, cudaStream_t s);

@@ -36,6 +36,13 @@ def check_cut(mc, g, res, lam_ref):
     assert oracle.cut_weight(*g, side) == lam_ref
 
 
+def assert_root_labels(lab):
+    # union-find labels are roots: each points at the smallest vertex of its
+    # block, which points at itself
+    lab = np.asarray(lab)
+    assert (lab[lab] == lab).all() and (lab <= np.arange(len(lab))).all()
+
+
 def _random_tiny(rng, i):
     n = int(rng.integers(2, 15))
     kind = i % 4
@@ -103,6 +110,7 @@ def test_pr_parity(mc, level):
         lam = int(deg.min()) - int(rng.integers(0, 3))
         with mc.Graph(*g) as G:
             lab = G.pr_tests(lam, level)
+        assert_root_labels(lab)
         assert (lab == oracle.pr_tests(*g, lam, level)).all()
 
 
@@ -119,6 +127,7 @@ def test_capforest_round_is_safe(mc):
             with mc.Graph(*g) as G:
                 lab, lam_out, unions = G.capforest_round(int(deg.min()),
                                                          mc.options(region_budget=budget, seed=i))
+            assert_root_labels(lab)
             assert lam_out >= lam_g
             roots, lab2 = np.unique(lab, return_inverse=True)
             if len(roots) == 1:
@@ -137,6 +146,7 @@ def test_capforest_round_medium_safe(mc):
         deg = oracle.degrees(*g)
         with mc.Graph(*g) as G:
             lab, lam_out, unions = G.capforest_round(int(deg.min()))
+        assert_root_labels(lab)
         assert unions > 0
         roots, lab2 = np.unique(lab, return_inverse=True)
         if len(roots) == 1:
@@ -319,6 +329,7 @@ def test_capforest_full_scan_safe_and_progresses(mc):
             lab, lam_out, unions = G.capforest_full(bound, start=i % n)
             lab2_again, lam2, un2 = G.capforest_full(bound, start=i % n)
         assert (lab == lab2_again).all() and lam_out == lam2 and unions == un2  # deterministic
+        assert_root_labels(lab)
         assert lam_out >= lam_g
         if lam_out == bound and lam_g > 0:
             assert unions >= 1
@@ -329,3 +340,17 @@ def test_capforest_full_scan_safe_and_progresses(mc):
         crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
         lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
         assert min(lam_out, lam_c) == lam_g, (i, lam_out, lam_c, lam_g)
+
+
+def test_full_scan_deterministic_on_ties(mc):
+    # unit weights make many equal keys; the scan order among them (and so
+    # the set of unions) must not depend on hardware arbitration
+    for g in (graphgen.planted(2), graphgen.rhg(4, 1 << 13, 20.0), graphgen.cycle(300),
+              graphgen.rhg(6, 1 << 16, 24.0)):
+        with mc.Graph(*g) as G:
+            lam = int(G.degrees().min())
+            runs = [G.capforest_full(lam, start=5) for _ in range(6)]
+        for lab, lo, un in runs:
+            assert_root_labels(lab)
+        for lab, lo, un in runs[1:]:
+            assert (lab == runs[0][0]).all() and lo == runs[0][1] and un == runs[0][2]
