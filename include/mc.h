@@ -205,6 +205,39 @@ int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *lab
  * kernel source); labels n int32.                                         */
 int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *labels);
 
+/* ---- allocation-free full scan -------------------------------------------
+ * mc_capforest_full_noalloc -- the full CAPFOREST scan of
+ * mc_step_capforest_full without any device allocation, for callers that
+ * cannot allocate device memory while running: code that forbids allocation
+ * after start-up (a cudaMalloc can synchronise the device or fail on a
+ * fragmented heap) or a process whose device memory is held by another
+ * allocator.  The paper has no counterpart; it is an interface convenience.
+ *   n, arcs    vertices (1..MC_NOALLOC_MAX_N) and arcs (0..MC_NOALLOC_MAX_ARCS)
+ *   row_ptr    device int32[n+1] offsets
+ *   adj        device int32[2*arcs], 8-byte aligned: (neighbour, weight) per
+ *              arc, the layout of mc_graph_export's col/w interleaved; every
+ *              edge in both rows, weights >= 1, no self-loops
+ *   lam        the bound lambda-hat (> 0) the scan certifies against
+ *   start      start vertex in [0, n)
+ *   labels     device int32[n] output: smallest vertex of each vertex's block
+ *              after the scan's unions
+ *   lam_out, unions_out  host, may be NULL: bound after the scan's alpha
+ *              updates, and the number of unions
+ *   cuda_stream  stream to run on (NULL = default stream); the call returns
+ *              after the work has finished
+ * All scratch (about 3 MB) is one static device array that each GPU which
+ * loads the library keeps until exit.  The first call on a device looks up
+ * its address (cudaGetSymbolAddress) -- make that call before any stream
+ * capture.  Calls share the array: overlapping calls on one device race and
+ * must be serialised by the caller.  Sizes beyond the limits below return
+ * MC_EINVAL before any device work.
+ */
+#define MC_NOALLOC_MAX_N 32768
+#define MC_NOALLOC_MAX_ARCS 262144
+int mc_capforest_full_noalloc(int32_t n, int64_t arcs, const int32_t *row_ptr, const int32_t *adj,
+                              int64_t lam, int32_t start, int32_t *labels, int64_t *lam_out,
+                              int64_t *unions_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -599,4 +599,27 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
     return MC_OK;
 }
 
+// The full-scan kernel on caller-provided state (used by the allocation-free
+// entry point): par = union-find parents (initialised by the caller), T and
+// r zeroed, st->lam and st->scan_ids set, a pool of `pool` entries each for
+// eslot / enext.
+int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *st, i64 *rec_alpha,
+                       int *rec_len, int *r, int *eslot, int *enext, int pool, int start,
+                       cudaStream_t s) {
+    ScanArgs A;
+    A.g = g;
+    A.par = par;
+    A.T = T;
+    A.order = order;
+    A.st = st;
+    A.rec_alpha = rec_alpha;
+    A.rec_len = rec_len;
+    A.perm_a = 1;
+    A.perm_b = 0;
+    A.limit = 0;
+    ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, r, eslot, enext, pool, 0);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 }  // namespace mc

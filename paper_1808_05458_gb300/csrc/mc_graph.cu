@@ -538,4 +538,11 @@ int iota_i32(int *a, int n, cudaStream_t s) {
     return MC_OK;
 }
 
+// flatten a caller-provided union-find array: root[v] = root of v
+int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s) {
+    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(par, root, cnt, n);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 }  // namespace mc

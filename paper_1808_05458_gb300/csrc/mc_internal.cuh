@@ -202,6 +202,11 @@ int side_canon(Work &w, int n0, cudaStream_t s);
 int iota_i32(int *a, int n, cudaStream_t s);
 const std::string &error_detail();
 
+int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *st, i64 *rec_alpha,
+                       int *rec_len, int *r, int *eslot, int *enext, int pool, int start,
+                       cudaStream_t s);
+int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s);
+
 // label propagation sweeps on g into labels (int32[n])
 int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cudaStream_t s);
 

@@ -63,7 +63,7 @@ _lib = None
 EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_graph_size",
            "mc_min_cut", "mc_batch_min_cut", "mc_strerror", "mc_graph_export",
            "mc_step_degrees", "mc_step_contract", "mc_step_pr", "mc_step_capforest",
-           "mc_step_capforest_full", "mc_step_label_prop")
+           "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc")
 
 
 def library_path() -> str:
@@ -97,6 +97,7 @@ def load_library():
     lib.mc_step_capforest.argtypes = [vp, i64, P(McOptions), vp, P(i64), P(i64)]
     lib.mc_step_capforest_full.argtypes = [vp, i64, i32, vp, P(i64), P(i64)]
     lib.mc_step_label_prop.argtypes = [vp, i32, u64, vp]
+    lib.mc_capforest_full_noalloc.argtypes = [i32, i64, vp, vp, i64, i32, vp, P(i64), P(i64), vp]
     for f in EXPORTS:
         if f != "mc_strerror":
             getattr(lib, f).restype = ctypes.c_int
@@ -274,6 +275,28 @@ class Graph:
         _check(load_library().mc_step_label_prop(self._h, iters, seed, _ptr(lab)),
                "mc_step_label_prop")
         return lab
+
+
+NOALLOC_MAX_N = 32768
+NOALLOC_MAX_ARCS = 262144
+
+
+def capforest_full_noalloc(row_ptr, adj, lam: int, start: int, labels, stream=None):
+    """Allocation-free full CAPFOREST scan (``mc_capforest_full_noalloc``).
+
+    ``row_ptr`` (int32, n+1), ``adj`` (int32, 2*arcs interleaved neighbour /
+    weight) and ``labels`` (int32, n, output) are CUDA tensors; nothing is
+    allocated on the device.  Returns (lambda-hat after the scan, unions).
+    """
+    n = row_ptr.numel() - 1
+    arcs = adj.numel() // 2
+    lo, un = ctypes.c_int64(), ctypes.c_int64()
+    s = ctypes.c_void_p(stream) if stream else None
+    _check(load_library().mc_capforest_full_noalloc(
+        n, arcs, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(adj.data_ptr()), lam, start,
+        ctypes.c_void_p(labels.data_ptr()), ctypes.byref(lo), ctypes.byref(un), s),
+        "mc_capforest_full_noalloc")
+    return lo.value, un.value
 
 
 def min_cut(row_ptr, col, w, **opt) -> MinCut:
