@@ -42,9 +42,9 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def make_graph(seed):
+def make_graph(seed, log2n=20):
     import graphgen
-    return graphgen.rhg(seed, 1 << 20, 32.0, 5.0)
+    return graphgen.rhg(seed, 1 << log2n, 32.0, 5.0)
 
 
 class ClockSampler:
@@ -143,7 +143,7 @@ def run_reference(args, rank, world):
     """Reference arm: the CPU oracle (sequential NOI) on the host cores."""
     if rank != 0:
         return 0
-    g = make_graph(args.seed)
+    g = make_graph(args.seed, args.rhg_log2)
     m = len(g[1]) // 2
     import oracle
     oracle.build()
@@ -187,7 +187,7 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    g = make_graph(args.seed)
+    g = make_graph(args.seed, args.rhg_log2)
     rp, col, w = g
     n = len(rp) - 1
     m = len(col) // 2
@@ -278,7 +278,8 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": value / PAPER_EDGES_PER_S, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "lambda": lam,
+        "config": {"workload": WORKLOAD if args.rhg_log2 == 20 else
+                   f"rhg_n2^{args.rhg_log2}_deg32_gamma5_lcc_unit", "n": n, "m": m, "lambda": lam,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; CSR 402 MB > L2",
                    "rounds": s0["rounds"], "fallback_rounds": s0["fallback_rounds"],
@@ -308,6 +309,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--rhg-log2", type=int, default=20,
+                    help="log2 of the RHG point count (20 = the benchmark workload; smaller "
+                         "sizes are for profiling captures)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
