@@ -260,7 +260,9 @@ def run_gpu(args, rank, world, local_rank):
     roofline = {"kernel": "k_capforest (concurrent capped CAPFOREST scans)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                # one capture on RHG n=2^19 round 0, scaled by algorithmic bytes
+                "traffic": tr["traffic_over_alg"] * per_launch_bytes if tr else None,
+                "traffic_source": "profiles/k_capforest_rhg2e19.md" if tr else None,
                 "alg_bytes_per_launch": per_launch_bytes,
                 "ms_per_launch": per_launch_s * 1000.0,
                 "share_of_step": scan_ms / max(1e-9, total_ms)}
