@@ -153,13 +153,33 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,
  *   bitmaps   NULL, or per-graph side bitmaps: graph g's ceil(n_g/32) words
  *             start at bitmap_word_off[g] (host)
  *   bitmap_word_off  G+1 int64, required when bitmaps is non-NULL
- * Every graph must be connected or not, weights >= 0, symmetric.
- * Errors as mc_graph_create / mc_min_cut, for the first failing graph.
+ * One kernel launch solves the whole batch: one warp per graph, graphs
+ * taken largest first (Alg. 2 per graph with full capped scans, PR1/PR2 and
+ * in-warp contraction).  Inputs must be symmetric (not checked here);
+ * self-loops and zero weights are dropped and parallel arcs merged; a
+ * disconnected graph gets lambda 0.  stats: n_input/m_input are totals,
+ * ms_total is the kernel's device time.
+ * Errors: MC_EINVAL (n_g < 2, bad offsets, neighbour out of range, negative
+ * weight), MC_EOVERFLOW, MC_ENOMEM, MC_ECUDA, MC_EINTERNAL -- the first
+ * failing graph's code.
  */
 int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
                      const int32_t *row_ptr, const int32_t *col, const int32_t *w,
                      const mc_options *opt, int64_t *lambdas, uint32_t *bitmaps,
                      const int64_t *bitmap_word_off, mc_stats *stats);
+
+/*
+ * mc_batch_autotune -- time every batched-kernel shape (warps per block x
+ * vertices whose scan state fits in shared memory per warp) on this batch,
+ * keep the fastest for later mc_batch_min_cut calls on the current device
+ * of this process, and report it.  Arguments as mc_batch_min_cut;
+ * ms_per_shape (max_shapes entries, may be NULL) receives each shape's
+ * kernel time.  The shapes' results are not returned.
+ */
+int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
+                      const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                      const mc_options *opt, int32_t *best_shape, double *ms_per_shape,
+                      int32_t max_shapes);
 
 /* Message for an error code (thread-local detail for MC_ECUDA). */
 const char *mc_strerror(int code);

@@ -375,31 +375,48 @@ int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off, 
                      const int32_t *col, const int32_t *w, const mc_options *opt, int64_t *lambdas,
                      uint32_t *bitmaps, const int64_t *bitmap_word_off, mc_stats *stats) {
     if (G < 0 || !vtx_off || !arc_off || !row_ptr || !lambdas) return MC_EINVAL;
+    if (G > 0 && arc_off[G] > 0 && (!col || !w)) return MC_EINVAL;
     if (bitmaps && !bitmap_word_off) return MC_EINVAL;
-    mc_stats agg;
-    memset(&agg, 0, sizeof(agg));
-    for (int32_t k = 0; k < G; ++k) {
-        const int64_t n = vtx_off[k + 1] - vtx_off[k];
-        if (n < 2 || n > 0x7FFFFFFF) return MC_EINVAL;
-        const int32_t *rp = row_ptr + vtx_off[k] + k;
-        const int64_t a0 = arc_off[k];
-        if (rp[n] != (int32_t)(arc_off[k + 1] - a0)) return MC_EINVAL;
-        mc_graph *g = nullptr;
-        int rc = mc_graph_create((int32_t)n, rp, col + a0, w + a0, 0, &g);
-        if (rc != MC_OK) return rc;
-        mc_stats st;
-        rc = mc_min_cut(g, opt, &lambdas[k], bitmaps ? bitmaps + bitmap_word_off[k] : nullptr, &st);
-        mc_graph_destroy(g);
-        if (rc != MC_OK) return rc;
-        agg.rounds += st.rounds;
-        agg.fallback_rounds += st.fallback_rounds;
-        agg.n_input += st.n_input;
-        agg.m_input += st.m_input;
-        agg.ms_total += st.ms_total;
-        agg.bytes_alg += st.bytes_alg;
-        agg.scanned_arcs += st.scanned_arcs;
+    mc_options o;
+    if (opt) o = *opt; else mc_options_default(&o);
+    const long long l0 = g_launches;
+    double ms = 0;
+    int rc = batch_solve(G, (const long long *)vtx_off, (const long long *)arc_off, row_ptr, col, w, o,
+                         (long long *)lambdas, bitmaps, (const long long *)bitmap_word_off, -1, &ms);
+    if (rc != MC_OK) return rc;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->n_input = G > 0 ? vtx_off[G] : 0;
+        stats->m_input = G > 0 ? arc_off[G] / 2 : 0;
+        stats->ms_total = ms;
+        stats->kernel_launches = g_launches - l0;
     }
-    if (stats) *stats = agg;
+    return MC_OK;
+}
+
+int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off, const int32_t *row_ptr,
+                      const int32_t *col, const int32_t *w, const mc_options *opt, int32_t *best_shape,
+                      double *ms_per_shape, int32_t max_shapes) {
+    if (G < 1 || !vtx_off || !arc_off || !row_ptr || !col || !w) return MC_EINVAL;
+    mc_options o;
+    if (opt) o = *opt; else mc_options_default(&o);
+    std::vector<long long> lam((size_t)G);
+    const int ns = batch_shapes();
+    int best = 0;
+    double best_ms = 1e300;
+    for (int k = 0; k < ns; ++k) {
+        double t = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            double ms = 0;
+            MC_TRY(batch_solve(G, (const long long *)vtx_off, (const long long *)arc_off, row_ptr, col, w, o,
+                               lam.data(), nullptr, nullptr, k, &ms));
+            if (ms < t) t = ms;
+        }
+        if (ms_per_shape && k < max_shapes) ms_per_shape[k] = t;
+        if (t < best_ms) { best_ms = t; best = k; }
+    }
+    batch_set_shape(best);
+    if (best_shape) *best_shape = best;
     return MC_OK;
 }
 

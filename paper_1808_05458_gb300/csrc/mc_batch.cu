@@ -1,0 +1,685 @@
+// mc_batch.cu -- many independent graphs at once, one warp per graph.
+//
+// Each warp runs the whole exact loop of Alg. 2 on its graph, entirely in
+// its own scratch (shared memory for the scan's r-values and queue when the
+// graph is small enough, a per-warp global slice otherwise):
+//   canonicalise (merge parallel arcs, drop self-loops and zero weights) ->
+//   components (lambda = 0 if disconnected) -> lambda-hat = delta ->
+//   rounds of { Padberg-Rinaldi PR1/PR2 + degree-2 tie rule; one full capped
+//   CAPFOREST scan (Alg. 3 with the Lemma 1 cap, from a seeded start); in-warp
+//   contraction (Sec. 2.1) with the lambda-hat clamp; lambda-hat = min(., delta) }
+//   until one vertex is left; the side is kept as in Sec. 3.3.
+// The in-warp contraction is a stable counting sort of the arcs by their new
+// source block (lanes of one chunk ranked with match_any, so the result is
+// deterministic), then a per-row merge of parallel arcs through a marker
+// array over the new vertices (first occurrence kept, weights added with the
+// clamp), compacted into the next CSR.
+// Warps take graphs from a shared queue ordered by size (largest first).
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "mc_internal.cuh"
+#include "mc_scan.cuh"
+
+namespace mc {
+
+namespace {
+
+constexpr int kBNB = 256;  // queue buckets per warp
+
+template <int SN>
+struct WarpSmem {
+    int r[SN];
+    unsigned short eslot[SN + SN / 2];
+    unsigned short enext[SN + SN / 2];
+    int head[kBNB];
+    int tail[kBNB];
+    u32 bits[kBNB / 32];
+    int top;
+};
+
+// per-warp global scratch, sized for the largest graph of the batch
+struct Scratch {
+    int *rpA, *rpB, *rpT, *srcA, *srcB, *eslot, *enext;
+    int2 *adjA, *adjB, *adjT;
+    i64 *deg;
+    int *par, *root, *lab, *cnt, *mark, *T, *order, *orig, *rg;
+    u32 *best;
+    Status *st;
+    i64 *rec_alpha;
+    int *rec_len;
+};
+
+struct Layout {
+    int nmax;
+    long long amax;
+    size_t bytes;  // per warp
+    // byte offsets
+    size_t rpA, rpB, rpT, srcA, srcB, eslot, enext, adjA, adjB, adjT, deg, par, root, lab, cnt, mark, T, order,
+        orig, rg, best, st, rec_alpha, rec_len;
+};
+
+static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+static Layout make_layout(int nmax, long long amax) {
+    Layout L;
+    L.nmax = nmax;
+    L.amax = amax;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    const size_t N1 = (size_t)nmax + 1, A = (size_t)amax + 2;
+    L.rpA = take(4 * N1); L.rpB = take(4 * N1); L.rpT = take(4 * N1);
+    L.srcA = take(4 * A); L.srcB = take(4 * A);
+    L.eslot = take(4 * A); L.enext = take(4 * A);
+    L.adjA = take(8 * A); L.adjB = take(8 * A); L.adjT = take(8 * A);
+    L.deg = take(8 * N1);
+    L.par = take(4 * N1); L.root = take(4 * N1); L.lab = take(4 * N1); L.cnt = take(4 * N1);
+    L.mark = take(4 * N1); L.T = take(4 * N1); L.order = take(4 * N1); L.orig = take(4 * N1);
+    L.rg = take(4 * N1);
+    L.best = take(4 * (N1 / 32 + 2));
+    L.st = take(sizeof(Status));
+    L.rec_alpha = take(8 * 4);
+    L.rec_len = take(4 * 4);
+    L.bytes = o;
+    return L;
+}
+
+__device__ Scratch scratch_of(unsigned char *base, const Layout &L) {
+    Scratch S;
+    S.rpA = (int *)(base + L.rpA); S.rpB = (int *)(base + L.rpB); S.rpT = (int *)(base + L.rpT);
+    S.srcA = (int *)(base + L.srcA); S.srcB = (int *)(base + L.srcB);
+    S.eslot = (int *)(base + L.eslot); S.enext = (int *)(base + L.enext);
+    S.adjA = (int2 *)(base + L.adjA); S.adjB = (int2 *)(base + L.adjB); S.adjT = (int2 *)(base + L.adjT);
+    S.deg = (i64 *)(base + L.deg);
+    S.par = (int *)(base + L.par); S.root = (int *)(base + L.root); S.lab = (int *)(base + L.lab);
+    S.cnt = (int *)(base + L.cnt); S.mark = (int *)(base + L.mark); S.T = (int *)(base + L.T);
+    S.order = (int *)(base + L.order); S.orig = (int *)(base + L.orig); S.rg = (int *)(base + L.rg);
+    S.best = (u32 *)(base + L.best);
+    S.st = (Status *)(base + L.st);
+    S.rec_alpha = (i64 *)(base + L.rec_alpha);
+    S.rec_len = (int *)(base + L.rec_len);
+    return S;
+}
+
+struct BatchIn {
+    int G;
+    const long long *voff, *aoff;
+    const int *rp, *col, *w;
+    const int *order;  // graphs, largest first
+    long long *lam_out;
+    u32 *bits_out;                // may be null
+    const long long *bits_off;    // word offsets, may be null
+    int *err_out;
+    int *next;                    // work counter
+    unsigned char *scratch;
+    Layout L;
+    u64 seed;
+    int pr_level;
+    int fifo;
+};
+
+// ------------------------------------------------------------ warp tools --
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// exclusive scan of cnt[0..n) into out[0..n], out[n] = total; returns total
+__device__ int warp_excl_scan(const int *cnt, int *out, int n) {
+    const int lane = lane_id();
+    int carry = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const int v = i < n ? cnt[i] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (i < n) out[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) out[n] = carry;
+    __syncwarp();
+    return carry;
+}
+
+// weight add with saturation at `clamp`; sets *ovf if a sum passes INT32_MAX
+__device__ __forceinline__ void add_clamped(int *p, int w, long long clamp, int *ovf) {
+    int old = *p, assumed;
+    do {
+        assumed = old;
+        long long s = (long long)assumed + w;
+        if (s > kInt32Max) *ovf = 1;
+        int nv = (int)(s > clamp ? clamp : s);
+        old = atomicCAS(p, assumed, nv);
+    } while (old != assumed);
+}
+
+// (minimum degree, smallest vertex with it) over deg[0..n)
+__device__ void warp_min_deg(const i64 *deg, int n, long long *md, int *arg) {
+    const int lane = lane_id();
+    long long best = LLONG_MAX;
+    int bi = INT_MAX;
+    for (int v = lane; v < n; v += 32) {
+        const long long d = deg[v];
+        if (d < best) { best = d; bi = v; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    *md = best;
+    *arg = bi;
+}
+
+// Contract (in_src, in_adj)[0..m) over n vertices by labels lab[] in [0, nc)
+// into the CSR (rp, src, adj, deg) with merged weights clamped to `clamp`.
+// Uses tmp_rp / tmp_adj for the row-sorted copy and S.cnt / S.mark.
+// Returns the arc count of the result.
+__device__ long long warp_contract(const int *in_src, const int2 *in_adj, long long m, const int *lab,
+                                   int nc, long long clamp, int *tmp_rp, int2 *tmp_adj, int *rp,
+                                   int *src, int2 *adj, i64 *deg, int *cnt, int *mark, int *ovf) {
+    const int lane = lane_id();
+    for (int a = lane; a < nc; a += 32) cnt[a] = 0;
+    __syncwarp();
+    for (long long i0 = 0; i0 < m; i0 += 32) {
+        const long long i = i0 + lane;
+        if (i < m) {
+            const int a = lab[in_src[i]], b = lab[in_adj[i].x];
+            if (a != b) atomicAdd(&cnt[a], 1);
+        }
+    }
+    __syncwarp();
+    warp_excl_scan(cnt, tmp_rp, nc);
+    // stable scatter: cursor per row in mark[], lanes of a chunk ranked by match_any
+    for (int a = lane; a < nc; a += 32) mark[a] = tmp_rp[a];
+    __syncwarp();
+    for (long long i0 = 0; i0 < m; i0 += 32) {
+        const long long i = i0 + lane;
+        int a = -1 - lane, b = 0, c = 0;
+        if (i < m) {
+            a = lab[in_src[i]];
+            b = lab[in_adj[i].x];
+            c = in_adj[i].y;
+            if (a == b) a = -1 - lane;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, a);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int base = 0;
+        if (a >= 0) base = mark[a];
+        __syncwarp();
+        if (a >= 0) {
+            tmp_adj[base + rank] = make_int2(b, c);
+            if (rank == 0) mark[a] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+    // merge parallel arcs row by row: first occurrence keeps the arc
+    for (int a = lane; a < nc; a += 32) mark[a] = INT_MAX;
+    __syncwarp();
+    long long out = 0;
+    for (int a = 0; a < nc; ++a) {
+        const int lo = tmp_rp[a], hi = tmp_rp[a + 1];
+        if (lane == 0) rp[a] = (int)out;
+        for (int e = lo + lane; e < hi; e += 32) atomicMin(&mark[tmp_adj[e].x], e);
+        __syncwarp();
+        for (int e = lo + lane; e < hi; e += 32) {
+            const int2 x = tmp_adj[e];
+            const int rep = mark[x.x];
+            if (rep != e) add_clamped(&tmp_adj[rep].y, x.y, clamp, ovf);
+        }
+        __syncwarp();
+        long long dsum = 0;
+        for (int e0 = lo; e0 < hi; e0 += 32) {
+            const int e = e0 + lane;
+            bool keep = false;
+            int2 x = make_int2(0, 0);
+            if (e < hi) {
+                x = tmp_adj[e];
+                keep = mark[x.x] == e;
+            }
+            const unsigned kb = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const long long pos = out + __popc(kb & ((1u << lane) - 1u));
+                const int wv = (int)((long long)x.y > clamp ? clamp : (long long)x.y);
+                adj[pos] = make_int2(x.x, wv);
+                src[pos] = a;
+                dsum += wv;
+            }
+            out += __popc(kb);
+        }
+        __syncwarp();
+        for (int e = lo + lane; e < hi; e += 32) mark[tmp_adj[e].x] = INT_MAX;
+        dsum = warp_sum_ll(dsum);
+        if (lane == 0) deg[a] = dsum;
+        __syncwarp();
+    }
+    if (lane == 0) rp[nc] = (int)out;
+    __syncwarp();
+    return out;
+}
+
+// flatten the union-find par[0..n) into root[] and number the blocks in
+// lab[] (order of the smallest member); returns the block count
+__device__ int warp_relabel(int *par, int *root, int *lab, int *cnt, int n) {
+    const int lane = lane_id();
+    for (int v = lane; v < n; v += 32) {
+        const int r = uf_find(par, v);
+        root[v] = r;
+        cnt[v] = r == v;
+    }
+    __syncwarp();
+    const int nc = warp_excl_scan(cnt, lab, n);
+    for (int v = lane; v < n; v += 32) {
+        const int r = root[v];
+        if (r != v) lab[v] = lab[r];
+    }
+    __syncwarp();
+    return nc;
+}
+
+template <class F>
+__device__ void warp_side_bits(u32 *bits, int n0, F f) {
+    const int lane = lane_id();
+    for (int v0 = 0; v0 < n0; v0 += 32) {
+        const int v = v0 + lane;
+        const bool b = v < n0 && f(v);
+        const unsigned m = __ballot_sync(0xffffffffu, b);
+        if (lane == 0) bits[v0 / 32] = m;
+    }
+    __syncwarp();
+}
+
+// one full capped CAPFOREST scan of the current graph (Alg. 3)
+template <int SN>
+__device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, int n, long long arcs,
+                               long long lam, int start, int fifo, Counters &cnt) {
+    const int lane = lane_id();
+    const bool in_smem = n <= SN;
+    int *r = in_smem ? sm.r : S.rg;
+    for (int v = lane; v < n; v += 32) { r[v] = 0; S.T[v] = 0; }
+    for (int b = lane; b < kBNB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
+    if (lane < kBNB / 32) sm.bits[lane] = 0;
+    if (lane == 0) {
+        sm.top = 0;
+        S.st->lam = lam;
+        S.st->scan_ids = 1;
+    }
+    __syncwarp();
+    const int C = (int)(lam < (long long)0x7FFFFFFD ? lam : (long long)0x7FFFFFFD);
+    if (in_smem) {
+        BucketQ<unsigned short, kBNB> q;
+        q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.eslot; q.enext = sm.enext;
+        q.top = &sm.top; q.cap = SN + SN / 2; q.C = C; q.coarse = C + 1 > kBNB; q.fifo = fifo != 0;
+        DenseTable tab{r, n};
+        scan_one<DenseTable, BucketQ<unsigned short, kBNB>>(A, tab, q, start, 1, cnt);
+    } else {
+        BucketQ<int, kBNB> q;
+        q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = S.eslot; q.enext = S.enext;
+        q.top = &sm.top; q.cap = (int)(arcs + 2); q.C = C; q.coarse = C + 1 > kBNB; q.fifo = fifo != 0;
+        DenseTable tab{r, 0};
+        scan_one<DenseTable, BucketQ<int, kBNB>>(A, tab, q, start, 1, cnt);
+    }
+    __syncwarp();
+}
+
+template <int SN>
+__device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm) {
+    const int lane = lane_id();
+    const long long v0 = B.voff[gi];
+    const int n0 = (int)(B.voff[gi + 1] - v0);
+    const int *rp_in = B.rp + v0 + gi;
+    const long long a0 = B.aoff[gi];
+    const int *col_in = B.col + a0, *w_in = B.w + a0;
+    int err = 0;
+    int ovf = 0;
+
+    // raw arcs -> (srcB, adjB), dropping self-loops and zero weights
+    long long m = 0;
+    for (int u = 0; u < n0; ++u) {
+        const int lo = rp_in[u], hi = rp_in[u + 1];
+        for (int e0 = lo; e0 < hi; e0 += 32) {
+            const int e = e0 + lane;
+            bool keep = false;
+            int v = 0, c = 0;
+            if (e < hi) {
+                v = col_in[e];
+                c = w_in[e];
+                if (v < 0 || v >= n0) err = MC_EINVAL;
+                else if (c < 0) err = MC_EINVAL;
+                else keep = v != u && c > 0;
+            }
+            const unsigned kb = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const long long pos = m + __popc(kb & ((1u << lane) - 1u));
+                S.srcB[pos] = u;
+                S.adjB[pos] = make_int2(v, c);
+            }
+            m += __popc(kb);
+        }
+    }
+    err = __reduce_or_sync(0xffffffffu, err);
+    // canonical CSR in A (identity labels)
+    for (int v = lane; v < n0; v += 32) S.lab[v] = v;
+    __syncwarp();
+    long long arcs = warp_contract(S.srcB, S.adjB, m, S.lab, n0, kInt32Max, S.rpT, S.adjT, S.rpA,
+                                   S.srcA, S.adjA, S.deg, S.cnt, S.mark, &ovf);
+    if (__reduce_or_sync(0xffffffffu, ovf)) err = MC_EOVERFLOW;
+
+    long long lam = 0;
+    if (!err) {
+        // components
+        for (int v = lane; v < n0; v += 32) S.par[v] = v;
+        __syncwarp();
+        for (long long i = lane; i < arcs; i += 32) {
+            const int u = S.srcA[i], v = S.adjA[i].x;
+            if (u < v) uf_union(S.par, u, v);
+        }
+        __syncwarp();
+        const int ncomp = warp_relabel(S.par, S.root, S.lab, S.cnt, n0);
+        if (ncomp > 1) {
+            const int r0 = S.root[0];
+            warp_side_bits(S.best, n0, [&](int v) { return S.root[v] != r0; });
+            lam = 0;
+        } else {
+            int arg = 0;
+            warp_min_deg(S.deg, n0, &lam, &arg);
+            if (lam >= 0x7FFFFFFD) err = MC_EOVERFLOW;
+            warp_side_bits(S.best, n0, [&](int v) { return v == arg; });
+            for (int v = lane; v < n0; v += 32) S.orig[v] = v;
+            __syncwarp();
+            int n = n0;
+            int *rpA = S.rpA, *srcA = S.srcA, *rpB = S.rpB, *srcB = S.srcB;
+            int2 *adjA = S.adjA, *adjB = S.adjB;
+            int round = 0, guard = 0;
+            while (!err && n >= 2 && lam > 0) {
+                if (++guard > 4 * n0 + 16) { err = MC_EINTERNAL; break; }
+                for (int v = lane; v < n; v += 32) S.par[v] = v;
+                __syncwarp();
+                long long un = 0;
+                // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
+                if (B.pr_level >= 1) {
+                    for (long long i = lane; i < arcs; i += 32) {
+                        const int u = srcA[i];
+                        const int2 e = adjA[i];
+                        if (u >= e.x) continue;
+                        const long long c = e.y, du = S.deg[u], dv = S.deg[e.x];
+                        const bool ok = c >= lam || (B.pr_level >= 2 && 2 * c > (du < dv ? du : dv));
+                        if (ok && uf_union(S.par, u, e.x)) ++un;
+                    }
+                    if (B.pr_level >= 2) {
+                        for (int u = lane; u < n; u += 32) {
+                            const int a = rpA[u];
+                            if (rpA[u + 1] - a != 2) continue;
+                            const int2 e0 = adjA[a], e1 = adjA[a + 1];
+                            if (e0.y == e1.y && uf_union(S.par, u, e0.x < e1.x ? e0.x : e1.x)) ++un;
+                        }
+                    }
+                    __syncwarp();
+                }
+                // one full capped CAPFOREST scan
+                ScanArgs A;
+                A.g.n = n; A.g.arcs = arcs; A.g.rp = rpA; A.g.src = srcA; A.g.adj = adjA; A.g.deg = S.deg;
+                A.par = S.par; A.T = S.T; A.order = S.order; A.st = S.st;
+                A.rec_alpha = S.rec_alpha; A.rec_len = S.rec_len; A.perm_a = 1; A.perm_b = 0; A.limit = 0;
+                const u64 h = splitmix64(B.seed ^ splitmix64(((u64)gi << 20) ^ (u64)round));
+                const int start = (int)(h % (u64)n);
+                Counters cnt;
+                warp_full_scan<SN>(A, sm, S, n, arcs, lam, start, B.fifo, cnt);
+                un += cnt.unions;
+                un = warp_sum_ll(un);
+                const long long lam2 = ld_volatile_i64(&S.st->lam);
+                if (lam2 < lam) {
+                    const int len = S.rec_len[1];
+                    warp_side_bits(S.best, n0, [&](int v) {
+                        const int c = S.orig[v];
+                        return S.T[c] == 1 && S.order[c] < len;
+                    });
+                    const long long before = lam;
+                    lam = lam2;
+                    if (un == 0) { ++round; (void)before; continue; }
+                }
+                if (un == 0) { err = MC_EINTERNAL; break; }
+                // contraction
+                const int nc = warp_relabel(S.par, S.root, S.lab, S.cnt, n);
+                // the result goes to the B buffers, then A and B swap roles
+                arcs = warp_contract(srcA, adjA, arcs, S.lab, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB,
+                                     S.deg, S.cnt, S.mark, &ovf);
+                for (int v = lane; v < n0; v += 32) S.orig[v] = S.lab[S.orig[v]];
+                __syncwarp();
+                {
+                    int *t = rpA; rpA = rpB; rpB = t;
+                    t = srcA; srcA = srcB; srcB = t;
+                    int2 *ta = adjA; adjA = adjB; adjB = ta;
+                }
+                n = nc;
+                if (n >= 2) {
+                    long long md;
+                    int arg;
+                    warp_min_deg(S.deg, n, &md, &arg);
+                    if (md < lam) {
+                        lam = md;
+                        warp_side_bits(S.best, n0, [&](int v) { return S.orig[v] == arg; });
+                    }
+                }
+                ++round;
+            }
+        }
+    }
+    if (lane == 0) {
+        B.lam_out[gi] = lam;
+        B.err_out[gi] = err;
+    }
+    if (B.bits_out && !err) {
+        u32 *dst = B.bits_out + B.bits_off[gi];
+        const int nw = (n0 + 31) / 32;
+        const bool flip = S.best[0] & 1u;
+        for (int i = lane; i < nw; i += 32) {
+            u32 v = flip ? ~S.best[i] : S.best[i];
+            if (i == nw - 1 && (n0 & 31)) v &= (1u << (n0 & 31)) - 1u;
+            dst[i] = v;
+        }
+    }
+    __syncwarp();
+}
+
+template <int WPB, int SN>
+__global__ void __launch_bounds__(WPB * 32) k_batch(BatchIn B) {
+    __shared__ WarpSmem<SN> smem[WPB];
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * WPB + wid;
+    Scratch S0 = scratch_of(B.scratch + (size_t)gw * B.L.bytes, B.L);
+    while (true) {
+        int k = 0;
+        if (lane_id() == 0) k = atomicAdd(B.next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= B.G) break;
+        solve_one<SN>(B, B.order[k], S0, smem[wid]);
+    }
+}
+
+// ------------------------------------------------------------ host side --
+struct BatchCtx {
+    unsigned char *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void *io = nullptr;
+    size_t io_bytes = 0;
+    cudaStream_t stream = nullptr;
+};
+std::mutex g_batch_mutex;
+BatchCtx g_batch[64];
+
+int grow(void **p, size_t *cur, size_t want, cudaStream_t s) {
+    if (*cur >= want) return MC_OK;
+    if (*p) {
+        cudaStreamSynchronize(s);
+        cudaFree(*p);
+        *p = nullptr;
+        *cur = 0;
+    }
+    MC_TRY(dev_alloc(p, want, s));
+    *cur = want;
+    return MC_OK;
+}
+
+template <int WPB, int SN>
+int launch_batch(const BatchIn &B, int warps, cudaStream_t s) {
+    const int blocks = (warps + WPB - 1) / WPB;
+    ++::mc::g_launches; k_batch<WPB, SN><<<blocks, WPB * 32, 0, s>>>(B);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+}  // namespace
+
+// batch configurations the autotuner chooses from: warps per block x shared
+// vertices per warp
+struct BatchShape {
+    int wpb, sn;
+};
+static const BatchShape kShapes[] = {{4, 1024}, {4, 2048}, {8, 512}, {8, 1024}, {2, 2048}};
+static int g_shape_choice = -1;  // -1: not tuned
+
+static int run_batch(int shape, BatchIn B, int warps, cudaStream_t s) {
+    const BatchShape sh = kShapes[shape];
+    if (sh.wpb == 4 && sh.sn == 1024) return launch_batch<4, 1024>(B, warps, s);
+    if (sh.wpb == 4 && sh.sn == 2048) return launch_batch<4, 2048>(B, warps, s);
+    if (sh.wpb == 8 && sh.sn == 512) return launch_batch<8, 512>(B, warps, s);
+    if (sh.wpb == 8 && sh.sn == 1024) return launch_batch<8, 1024>(B, warps, s);
+    return launch_batch<2, 2048>(B, warps, s);
+}
+
+static int blocks_per_sm(int shape) {
+    const BatchShape sh = kShapes[shape];
+    int b = 0;
+    cudaError_t e;
+    if (sh.wpb == 4 && sh.sn == 1024) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<4, 1024>, 128, 0);
+    else if (sh.wpb == 4 && sh.sn == 2048) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<4, 2048>, 128, 0);
+    else if (sh.wpb == 8 && sh.sn == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<8, 512>, 256, 0);
+    else if (sh.wpb == 8 && sh.sn == 1024) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<8, 1024>, 256, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<2, 2048>, 64, 0);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); b = 1; }
+    return b < 1 ? 1 : b;
+}
+
+int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const int *row_ptr,
+                const int *col, const int *w, const mc_options &o, long long *lambdas, u32 *bitmaps,
+                const long long *bitmap_word_off, int shape, double *ms_out) {
+    int dev = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MC_EINVAL;
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchCtx &ctx = g_batch[dev];
+    if (!ctx.stream) MC_CUDA(cudaStreamCreateWithFlags(&ctx.stream, cudaStreamNonBlocking));
+    cudaStream_t s = o.cuda_stream ? static_cast<cudaStream_t>(o.cuda_stream) : ctx.stream;
+
+    // host-side validation of the offsets
+    int nmax = 0;
+    long long amax = 0;
+    for (int k = 0; k < G; ++k) {
+        const long long n = vtx_off[k + 1] - vtx_off[k];
+        const long long a = arc_off[k + 1] - arc_off[k];
+        if (n < 2 || n > (1 << 24) || a < 0) return MC_EINVAL;
+        const int *rp = row_ptr + vtx_off[k] + k;
+        if (rp[0] != 0 || (long long)rp[n] != a) return MC_EINVAL;
+        for (long long v = 0; v < n; ++v)
+            if (rp[v + 1] < rp[v]) return MC_EINVAL;
+        nmax = std::max(nmax, (int)n);
+        amax = std::max(amax, a);
+    }
+    if (G == 0) return MC_OK;
+    std::vector<int> order((size_t)G);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return arc_off[x + 1] - arc_off[x] > arc_off[y + 1] - arc_off[y];
+    });
+
+    if (shape < 0) shape = g_shape_choice >= 0 ? g_shape_choice : 0;
+    const Layout L = make_layout(nmax, amax);
+    const int wpb = kShapes[shape].wpb;
+    const int warps_res = blocks_per_sm(shape) * wpb * num_sms();
+    int warps = std::min(warps_res, G);
+    warps = (warps + wpb - 1) / wpb * wpb;  // whole blocks: every warp owns a scratch slice
+
+    // device copies of the inputs and outputs in one buffer
+    const long long V = vtx_off[G], A = arc_off[G];
+    const long long bw = bitmaps ? bitmap_word_off[G] : 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t r = off; off += al(bytes); return r; };
+    const size_t o_voff = take(8 * (G + 1)), o_aoff = take(8 * (G + 1)), o_rp = take(4 * (V + G)),
+                 o_col = take(4 * (A > 0 ? A : 1)), o_w = take(4 * (A > 0 ? A : 1)),
+                 o_ord = take(4 * G), o_lam = take(8 * G), o_err = take(4 * G),
+                 o_bits = take(4 * (bw > 0 ? bw : 1)), o_boff = take(8 * (G + 1)), o_next = take(4);
+    MC_TRY(grow(&ctx.io, &ctx.io_bytes, off, s));
+    MC_TRY(grow(reinterpret_cast<void **>(&ctx.scratch), &ctx.scratch_bytes, L.bytes * (size_t)warps, s));
+    unsigned char *io = static_cast<unsigned char *>(ctx.io);
+    MC_CUDA(cudaMemcpyAsync(io + o_voff, vtx_off, 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(io + o_aoff, arc_off, 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(io + o_rp, row_ptr, 4 * (V + G), cudaMemcpyHostToDevice, s));
+    if (A > 0) {
+        MC_CUDA(cudaMemcpyAsync(io + o_col, col, 4 * A, cudaMemcpyHostToDevice, s));
+        MC_CUDA(cudaMemcpyAsync(io + o_w, w, 4 * A, cudaMemcpyHostToDevice, s));
+    }
+    MC_CUDA(cudaMemcpyAsync(io + o_ord, order.data(), 4 * (size_t)G, cudaMemcpyHostToDevice, s));
+    if (bitmaps) MC_CUDA(cudaMemcpyAsync(io + o_boff, bitmap_word_off, 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemsetAsync(io + o_next, 0, 4, s));
+
+    BatchIn B;
+    B.G = G;
+    B.voff = (const long long *)(io + o_voff);
+    B.aoff = (const long long *)(io + o_aoff);
+    B.rp = (const int *)(io + o_rp);
+    B.col = (const int *)(io + o_col);
+    B.w = (const int *)(io + o_w);
+    B.order = (const int *)(io + o_ord);
+    B.lam_out = (long long *)(io + o_lam);
+    B.err_out = (int *)(io + o_err);
+    B.bits_out = bitmaps ? (u32 *)(io + o_bits) : nullptr;
+    B.bits_off = bitmaps ? (const long long *)(io + o_boff) : nullptr;
+    B.next = (int *)(io + o_next);
+    B.scratch = ctx.scratch;
+    B.L = L;
+    B.seed = o.seed;
+    B.pr_level = o.pr_level;
+    B.fifo = o.pq_order == MC_PQ_FIFO;
+
+    cudaEvent_t ea, eb;
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventRecord(ea, s);
+    int rc = run_batch(shape, B, warps, s);
+    cudaEventRecord(eb, s);
+    if (rc != MC_OK) {
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        return rc;
+    }
+    std::vector<int> errs((size_t)G);
+    MC_CUDA(cudaMemcpyAsync(lambdas, io + o_lam, 8 * (size_t)G, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(errs.data(), io + o_err, 4 * (size_t)G, cudaMemcpyDeviceToHost, s));
+    if (bitmaps) MC_CUDA(cudaMemcpyAsync(bitmaps, io + o_bits, 4 * bw, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ea, eb);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (ms_out) *ms_out = ms;
+    for (int k = 0; k < G; ++k)
+        if (errs[k]) return errs[k];
+    return MC_OK;
+}
+
+int batch_shapes() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+void batch_set_shape(int shape) { g_shape_choice = shape; }
+int batch_get_shape() { return g_shape_choice; }
+
+}  // namespace mc

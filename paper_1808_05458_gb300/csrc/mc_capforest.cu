@@ -32,338 +32,9 @@
 #include <cstdio>
 
 #include "mc_internal.cuh"
+#include "mc_scan.cuh"
 
 namespace mc {
-
-constexpr int kDone = -1;
-constexpr int kSat = 0x7FFFFFFE;  // saturation value of r
-
-__device__ __forceinline__ int sat_add(int r, int c) { return r > kSat - c ? kSat : r + c; }
-
-// ------------------------------------------------------- bucket queue ----
-template <class Idx, int NB>
-struct BucketQ {
-    int *head;
-    int *tail;
-    u32 *bits;
-    Idx *eslot;
-    Idx *enext;
-    int *top;
-    int cap;   // pool entries
-    int C;     // key cap
-    bool coarse;
-    bool fifo;
-    static constexpr Idx NIL = (Idx)(-1);
-
-    __device__ __forceinline__ int bucket(int k) const {
-        return coarse ? (int)(((long long)k * NB) / ((long long)C + 1)) : k;
-    }
-    __device__ __forceinline__ int nxt(int e) const {
-        Idx v = enext[e];
-        return v == NIL ? -1 : (int)v;
-    }
-};
-
-// lanes with `want` push (slot s, key k); all lanes call.  false = no room.
-// Lanes pushing into the same bucket are chained in lane order (found with
-// match_any), so a push needs no atomics on list heads and the resulting
-// order -- hence the scan order among equal keys -- is deterministic.
-template <class Idx, int NB>
-__device__ bool pq_push(BucketQ<Idx, NB> &q, bool want, int s, int k) {
-    const int lane = threadIdx.x & 31;
-    unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return true;
-    int base = 0;
-    if (lane == 0) {
-        base = *q.top;
-        if (base + __popc(m) > q.cap) base = -1;
-        else *q.top = base + __popc(m);
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base < 0) return false;
-    const int e = base + __popc(m & ((1u << lane) - 1u));
-    const int b = want ? q.bucket(k) : -1 - lane;  // distinct dummies for idle lanes
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    const unsigned below = peers & ((1u << lane) - 1u);
-    const unsigned above = peers & ~((2u << lane) - 1u);
-    const int lo_lane = below ? 31 - __clz(below) : lane;  // next lower peer
-    const int hi_lane = above ? __ffs(above) - 1 : lane;   // next higher peer
-    const int e_lo = __shfl_sync(0xffffffffu, e, lo_lane);
-    const int e_hi = __shfl_sync(0xffffffffu, e, hi_lane);
-    const bool first = want && !below, last = want && !above;
-    int old = -1;
-    if (first) old = q.fifo ? q.tail[b] : q.head[b];
-    __syncwarp();
-    if (want) {
-        q.eslot[e] = (Idx)s;
-        if (!q.fifo) {
-            // LIFO: the highest lane becomes the head, each lane points down
-            q.enext[e] = first ? (old < 0 ? q.NIL : (Idx)old) : (Idx)e_lo;
-            if (last) q.head[b] = e;
-        } else {
-            // FIFO: append in lane order after the old tail
-            q.enext[e] = last ? q.NIL : (Idx)e_hi;
-            if (first) {
-                if (old < 0) q.head[b] = e;
-                else q.enext[old] = (Idx)e;
-            }
-            if (last) q.tail[b] = e;
-        }
-        if (first) atomicOr(&q.bits[b >> 5], 1u << (b & 31));
-    }
-    __syncwarp();
-    return true;
-}
-
-// warp-cooperative pop of a maximum key; returns the slot or -1 if empty.
-// rv[slot] is the slot's r value or kDone.
-template <class Idx, int NB>
-__device__ int pq_pop(BucketQ<Idx, NB> &q, const int *rv) {
-    const int lane = threadIdx.x & 31;
-    while (true) {
-        u32 word = lane < NB / 32 ? q.bits[lane] : 0u;
-        unsigned m = __ballot_sync(0xffffffffu, word != 0u);
-        if (!m) return -1;
-        int wl = 31 - __clz(m);
-        u32 wv = __shfl_sync(0xffffffffu, word, wl);
-        int b = wl * 32 + 31 - __clz(wv);
-        int found = -1;
-        if (lane == 0) {
-            int prev = -1, e = q.head[b];
-            int best = -1, bestprev = -1, bestkey = -1;
-            while (e >= 0) {
-                int s = (int)q.eslot[e];
-                int nx = q.nxt(e);
-                int r = rv[s];
-                int key = r < q.C ? r : q.C;
-                bool valid = r != kDone && q.bucket(key) == b;
-                if (!valid) {
-                    if (prev < 0) q.head[b] = nx; else q.enext[prev] = nx < 0 ? q.NIL : (Idx)nx;
-                    if (q.fifo && nx < 0) q.tail[b] = prev;
-                    e = nx;
-                    continue;
-                }
-                if (key > bestkey) { bestkey = key; best = e; bestprev = prev; }
-                if (!q.coarse || key == q.C) break;
-                prev = e;
-                e = nx;
-            }
-            if (best >= 0) {
-                int nx = q.nxt(best);
-                if (bestprev < 0) q.head[b] = nx; else q.enext[bestprev] = nx < 0 ? q.NIL : (Idx)nx;
-                if (q.fifo && nx < 0) q.tail[b] = bestprev;
-                found = (int)q.eslot[best];
-            }
-            if (q.head[b] < 0) {
-                q.bits[b >> 5] &= ~(1u << (b & 31));
-                q.tail[b] = -1;
-            }
-        }
-        found = __shfl_sync(0xffffffffu, found, 0);
-        __syncwarp();
-        if (found >= 0) return found;
-    }
-}
-
-// ------------------------------------------------------------- tables ----
-// shared-memory hash table of one warp's scan
-template <int HC, int NB>
-struct ScanSmem {
-    int key[HC];
-    int val[HC];
-    unsigned short eslot[2 * HC];
-    unsigned short enext[2 * HC];
-    int head[NB];
-    int tail[NB];
-    u32 bits[NB / 32];
-    int top;
-    int used;
-};
-
-template <int HC>
-struct LogHC;
-template <> struct LogHC<256> { static constexpr int v = 8; };
-template <> struct LogHC<512> { static constexpr int v = 9; };
-template <> struct LogHC<1024> { static constexpr int v = 10; };
-template <> struct LogHC<2048> { static constexpr int v = 11; };
-
-template <int HC, int NB>
-struct HashTable {
-    ScanSmem<HC, NB> *sm;
-    int limit;
-    __device__ __forceinline__ int *val() const { return sm->val; }
-    // slot of y, inserting it; -1 if the table refuses a new vertex
-    __device__ __forceinline__ int find(int y) const {
-        volatile int *key = sm->key;
-        unsigned h = ((unsigned)y * 2654435761u) >> (32 - LogHC<HC>::v);
-        for (int p = 0; p < HC; ++p) {
-            int k = key[h];
-            if (k == y) return (int)h;
-            if (k == -1) {
-                if (*(volatile int *)&sm->used >= limit) return -1;
-                int old = atomicCAS(&sm->key[h], -1, y);
-                if (old == -1) {
-                    atomicAdd(&sm->used, 1);
-                    sm->val[h] = 0;
-                    return (int)h;
-                }
-                if (old == y) return (int)h;
-            }
-            h = (h + 1) & (HC - 1);
-        }
-        return -1;
-    }
-    __device__ __forceinline__ int vertex(int slot) const { return sm->key[slot]; }
-};
-
-// dense table of the full scan: slot = vertex, r in global memory
-struct DenseTable {
-    int *r;
-    __device__ __forceinline__ int *val() const { return r; }
-    __device__ __forceinline__ int find(int y) const { return y; }
-    __device__ __forceinline__ int vertex(int slot) const { return slot; }
-};
-
-struct ScanArgs {
-    DevGraph g;
-    int *par, *T, *order;
-    Status *st;
-    i64 *rec_alpha;
-    int *rec_len;
-    u64 perm_a, perm_b;
-    int limit;
-};
-
-struct Counters {
-    long long arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
-};
-
-// garbage-collect a hash table's queue: rebuild every bucket list from the
-// live (touched, not DONE) slots
-template <int HC, int NB>
-__device__ void pq_rebuild(BucketQ<unsigned short, NB> &q, ScanSmem<HC, NB> &sm) {
-    const int lane = threadIdx.x & 31;
-    for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
-    if (lane < NB / 32) sm.bits[lane] = 0;
-    if (lane == 0) sm.top = 0;
-    __syncwarp();
-    for (int i0 = 0; i0 < HC; i0 += 32) {
-        int i = i0 + lane;
-        int r = sm.val[i];
-        bool live = sm.key[i] != -1 && r != kDone;
-        pq_push(q, live, i, r < q.C ? r : q.C);
-    }
-}
-
-// One scan of Alg. 1 from `start` with id `sid` and key cap C.
-template <class Table, class Q, bool HASHED>
-__device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt,
-                         void *smem_for_gc) {
-    const int lane = threadIdx.x & 31;
-    const int n = A.g.n;
-    const int C = q.C;
-    int *rv = tab.val();
-    {
-        int s = lane == 0 ? tab.find(start) : 0;
-        s = __shfl_sync(0xffffffffu, s, 0);
-        pq_push(q, lane == 0, s, 0);
-    }
-    long long alpha = 0, best = LLONG_MAX;
-    int nS = 0, best_len = 0;
-    bool alpha_ok = true, stop = false;
-    cnt.scans++;
-    while (!stop) {
-        int s = pq_pop(q, rv);
-        if (s < 0) break;
-        int x = tab.vertex(s);
-        int rx = rv[s];
-        __syncwarp();
-        int old = 0;
-        if (lane == 0) {
-            rv[s] = kDone;
-            old = atomicCAS(&A.T[x], 0, sid);
-        }
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old != 0) {
-            cnt.black++;
-            continue;
-        }
-        long long L = 0, dx = 0;
-        int a0 = 0, a1 = 0;
-        if (lane == 0) {
-            A.order[x] = nS;
-            L = ld_volatile_i64(&A.st->lam);
-            a0 = A.g.rp[x];
-            a1 = A.g.rp[x + 1];
-            dx = A.g.deg[x];
-        }
-        L = __shfl_sync(0xffffffffu, L, 0);
-        dx = __shfl_sync(0xffffffffu, dx, 0);
-        a0 = __shfl_sync(0xffffffffu, a0, 0);
-        a1 = __shfl_sync(0xffffffffu, a1, 0);
-        ++nS;
-        if (rx >= kSat) alpha_ok = false;
-        alpha += dx - 2LL * rx;
-        if (alpha_ok && nS < n && alpha < L) {
-            if (lane == 0) atomicMin(&A.st->lam, alpha);
-            if (alpha < best) { best = alpha; best_len = nS; }
-            L = alpha;
-        }
-        cnt.verts++;
-        cnt.arcs += a1 - a0;
-        for (int i0 = a0; i0 < a1; i0 += 32) {
-            int i = i0 + lane;
-            bool v = i < a1;
-            int y = 0, c = 0;
-            if (v) {
-                int2 e = A.g.adj[i];
-                y = e.x;
-                c = e.y;
-            }
-            int s2 = v ? tab.find(y) : -1;
-            // a full table refuses new vertices: the arc stays unscanned (its
-            // weight is 0 in Lemma 1's lowered graph) and alpha is no longer
-            // the cut of S, but the scan goes on over the vertices it holds
-            if (__any_sync(0xffffffffu, v && s2 < 0)) alpha_ok = false;
-            bool push = false;
-            int kn = 0;
-            if (s2 >= 0) {
-                int r_old = rv[s2];
-                if (r_old != kDone) {
-                    int r_new = sat_add(r_old, c);
-                    rv[s2] = r_new;
-                    // a certificate q = min(r, C) can only vouch for bounds <= C
-                    if ((long long)r_old < L && L <= (long long)r_new && L <= (long long)C) {
-                        if (uf_union(A.par, x, y)) cnt.unions++;
-                    }
-                    int ko = r_old < C ? r_old : C;
-                    kn = r_new < C ? r_new : C;
-                    push = r_old == 0 || q.bucket(kn) != q.bucket(ko);
-                }
-            }
-            if (!pq_push(q, push, s2, kn)) {
-                if constexpr (HASHED) {
-                    pq_rebuild(q, *reinterpret_cast<ScanSmem<Q::kHC, Q::kNB> *>(smem_for_gc));
-                } else {
-                    // the dense pool holds one entry per arc: cannot overflow
-                    stop = true;
-                    alpha_ok = false;
-                }
-            }
-        }
-        __syncwarp();
-    }
-    if (lane == 0) {
-        A.rec_alpha[sid] = best;
-        A.rec_len[sid] = best_len;
-    }
-}
-
-template <int HC_, int NB_>
-struct SmemQ : BucketQ<unsigned short, NB_> {
-    static constexpr int kHC = HC_;
-    static constexpr int kNB = NB_;
-};
 
 template <int WPB, int HC, int NB>
 __global__ void __launch_bounds__(WPB * 32)
@@ -420,7 +91,7 @@ k_capforest(ScanArgs A, int fifo) {
             __syncwarp();
             q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
             q.coarse = q.C + 1 > NB;
-            scan_one<HashTable<HC, NB>, SmemQ<HC, NB>, true>(A, tab, q, start, sid, cnt, &sm);
+            scan_one<HashTable<HC, NB>, SmemQ<HC, NB>>(A, tab, q, start, sid, cnt);
         }
     }
     // flush counters: unions are per lane, the rest are warp-uniform
@@ -464,11 +135,11 @@ k_capforest_full(ScanArgs A, int start, int *r, int *eslot, int *enext, int pool
     q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
     q.coarse = q.C + 1 > kFullNB;
     q.fifo = fifo != 0;
-    DenseTable tab{r};
+    DenseTable tab{r, 0};
     Counters cnt;
     int sid = 1;
     if (lane == 0) atomicAdd(&A.st->scan_ids, 1);
-    scan_one<DenseTable, BucketQ<int, kFullNB>, false>(A, tab, q, start, sid, cnt, nullptr);
+    scan_one<DenseTable, BucketQ<int, kFullNB>>(A, tab, q, start, sid, cnt);
     long long un = cnt.unions;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);

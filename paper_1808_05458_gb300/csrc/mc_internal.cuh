@@ -207,6 +207,15 @@ int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *
                        cudaStream_t s);
 int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s);
 
+// many graphs, one warp per graph (layout of mc_batch_min_cut, host arrays);
+// shape < 0 = the tuned or default configuration; *ms_out = kernel time
+int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const int *row_ptr,
+                const int *col, const int *w, const mc_options &o, long long *lambdas, u32 *bitmaps,
+                const long long *bitmap_word_off, int shape, double *ms_out);
+int batch_shapes();
+void batch_set_shape(int shape);
+int batch_get_shape();
+
 // label propagation sweeps on g into labels (int32[n])
 int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cudaStream_t s);
 

@@ -1,0 +1,370 @@
+// mc_scan.cuh -- one CAPFOREST scan (Alg. 1 / Alg. 3) run by one warp, with
+// its bucket priority queue and r-value tables.  Shared by the concurrent
+// scan kernel, the full-scan kernels and the per-graph warp solver; the
+// design notes are at the top of mc_capforest.cu.
+#pragma once
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+constexpr int kDone = -1;
+constexpr int kSat = 0x7FFFFFFE;  // saturation value of r
+
+__device__ __forceinline__ int sat_add(int r, int c) { return r > kSat - c ? kSat : r + c; }
+
+// ------------------------------------------------------- bucket queue ----
+template <class Idx, int NB>
+struct BucketQ {
+    int *head;
+    int *tail;
+    u32 *bits;
+    Idx *eslot;
+    Idx *enext;
+    int *top;
+    int cap;   // pool entries
+    int C;     // key cap
+    bool coarse;
+    bool fifo;
+    static constexpr Idx NIL = (Idx)(-1);
+    static constexpr int kNBuckets = NB;
+
+    __device__ __forceinline__ int bucket(int k) const {
+        return coarse ? (int)(((long long)k * NB) / ((long long)C + 1)) : k;
+    }
+    __device__ __forceinline__ int nxt(int e) const {
+        Idx v = enext[e];
+        return v == NIL ? -1 : (int)v;
+    }
+};
+
+// lanes with `want` push (slot s, key k); all lanes call.  false = no room.
+// Lanes pushing into the same bucket are chained in lane order (found with
+// match_any), so a push needs no atomics on list heads and the resulting
+// order -- hence the scan order among equal keys -- is deterministic.
+template <class Idx, int NB>
+__device__ bool pq_push(BucketQ<Idx, NB> &q, bool want, int s, int k) {
+    const int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return true;
+    int base = 0;
+    if (lane == 0) {
+        base = *q.top;
+        if (base + __popc(m) > q.cap) base = -1;
+        else *q.top = base + __popc(m);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base < 0) return false;
+    const int e = base + __popc(m & ((1u << lane) - 1u));
+    const int b = want ? q.bucket(k) : -1 - lane;  // distinct dummies for idle lanes
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const unsigned below = peers & ((1u << lane) - 1u);
+    const unsigned above = peers & ~((2u << lane) - 1u);
+    const int lo_lane = below ? 31 - __clz(below) : lane;  // next lower peer
+    const int hi_lane = above ? __ffs(above) - 1 : lane;   // next higher peer
+    const int e_lo = __shfl_sync(0xffffffffu, e, lo_lane);
+    const int e_hi = __shfl_sync(0xffffffffu, e, hi_lane);
+    const bool first = want && !below, last = want && !above;
+    int old = -1;
+    if (first) old = q.fifo ? q.tail[b] : q.head[b];
+    __syncwarp();
+    if (want) {
+        q.eslot[e] = (Idx)s;
+        if (!q.fifo) {
+            // LIFO: the highest lane becomes the head, each lane points down
+            q.enext[e] = first ? (old < 0 ? q.NIL : (Idx)old) : (Idx)e_lo;
+            if (last) q.head[b] = e;
+        } else {
+            // FIFO: append in lane order after the old tail
+            q.enext[e] = last ? q.NIL : (Idx)e_hi;
+            if (first) {
+                if (old < 0) q.head[b] = e;
+                else q.enext[old] = (Idx)e;
+            }
+            if (last) q.tail[b] = e;
+        }
+        if (first) atomicOr(&q.bits[b >> 5], 1u << (b & 31));
+    }
+    __syncwarp();
+    return true;
+}
+
+// warp-cooperative pop of a maximum key; returns the slot or -1 if empty.
+// rv[slot] is the slot's r value or kDone.
+template <class Idx, int NB>
+__device__ int pq_pop(BucketQ<Idx, NB> &q, const int *rv) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        u32 word = lane < NB / 32 ? q.bits[lane] : 0u;
+        unsigned m = __ballot_sync(0xffffffffu, word != 0u);
+        if (!m) return -1;
+        int wl = 31 - __clz(m);
+        u32 wv = __shfl_sync(0xffffffffu, word, wl);
+        int b = wl * 32 + 31 - __clz(wv);
+        int found = -1;
+        if (lane == 0) {
+            int prev = -1, e = q.head[b];
+            int best = -1, bestprev = -1, bestkey = -1;
+            while (e >= 0) {
+                int s = (int)q.eslot[e];
+                int nx = q.nxt(e);
+                int r = rv[s];
+                int key = r < q.C ? r : q.C;
+                bool valid = r != kDone && q.bucket(key) == b;
+                if (!valid) {
+                    if (prev < 0) q.head[b] = nx; else q.enext[prev] = nx < 0 ? q.NIL : (Idx)nx;
+                    if (q.fifo && nx < 0) q.tail[b] = prev;
+                    e = nx;
+                    continue;
+                }
+                if (key > bestkey) { bestkey = key; best = e; bestprev = prev; }
+                if (!q.coarse || key == q.C) break;
+                prev = e;
+                e = nx;
+            }
+            if (best >= 0) {
+                int nx = q.nxt(best);
+                if (bestprev < 0) q.head[b] = nx; else q.enext[bestprev] = nx < 0 ? q.NIL : (Idx)nx;
+                if (q.fifo && nx < 0) q.tail[b] = bestprev;
+                found = (int)q.eslot[best];
+            }
+            if (q.head[b] < 0) {
+                q.bits[b >> 5] &= ~(1u << (b & 31));
+                q.tail[b] = -1;
+            }
+        }
+        found = __shfl_sync(0xffffffffu, found, 0);
+        __syncwarp();
+        if (found >= 0) return found;
+    }
+}
+
+// ------------------------------------------------------------- tables ----
+// shared-memory hash table of one warp's scan
+template <int HC, int NB>
+struct ScanSmem {
+    int key[HC];
+    int val[HC];
+    unsigned short eslot[2 * HC];
+    unsigned short enext[2 * HC];
+    int head[NB];
+    int tail[NB];
+    u32 bits[NB / 32];
+    int top;
+    int used;
+};
+
+template <int HC>
+struct LogHC;
+template <> struct LogHC<256> { static constexpr int v = 8; };
+template <> struct LogHC<512> { static constexpr int v = 9; };
+template <> struct LogHC<1024> { static constexpr int v = 10; };
+template <> struct LogHC<2048> { static constexpr int v = 11; };
+
+template <int HC, int NB>
+struct HashTable {
+    ScanSmem<HC, NB> *sm;
+    int limit;
+    __device__ __forceinline__ int *val() const { return sm->val; }
+    // slot of y, inserting it; -1 if the table refuses a new vertex
+    __device__ __forceinline__ int find(int y) const {
+        volatile int *key = sm->key;
+        unsigned h = ((unsigned)y * 2654435761u) >> (32 - LogHC<HC>::v);
+        for (int p = 0; p < HC; ++p) {
+            int k = key[h];
+            if (k == y) return (int)h;
+            if (k == -1) {
+                if (*(volatile int *)&sm->used >= limit) return -1;
+                int old = atomicCAS(&sm->key[h], -1, y);
+                if (old == -1) {
+                    atomicAdd(&sm->used, 1);
+                    sm->val[h] = 0;
+                    return (int)h;
+                }
+                if (old == y) return (int)h;
+            }
+            h = (h + 1) & (HC - 1);
+        }
+        return -1;
+    }
+    __device__ __forceinline__ int vertex(int slot) const { return sm->key[slot]; }
+    template <class Q>
+    __device__ bool rebuild(Q &q) const;
+};
+
+// dense table of a full scan: slot = vertex, r in global or shared memory.
+// With `n_rebuild` > 0 a full pool is rebuilt from the n_rebuild vertices
+// (every touched, unscanned vertex has r > 0); otherwise the pool must be
+// large enough for every push (one per arc).
+struct DenseTable {
+    int *r;
+    int n_rebuild = 0;
+    __device__ __forceinline__ int *val() const { return r; }
+    __device__ __forceinline__ int find(int y) const { return y; }
+    __device__ __forceinline__ int vertex(int slot) const { return slot; }
+    template <class Q>
+    __device__ bool rebuild(Q &q) const;
+};
+
+struct ScanArgs {
+    DevGraph g;
+    int *par, *T, *order;
+    Status *st;
+    i64 *rec_alpha;
+    int *rec_len;
+    u64 perm_a, perm_b;
+    int limit;
+};
+
+struct Counters {
+    long long arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
+};
+
+// garbage-collect a hash table's queue: rebuild every bucket list from the
+// live (touched, not DONE) slots
+template <int HC, int NB>
+__device__ void pq_rebuild(BucketQ<unsigned short, NB> &q, ScanSmem<HC, NB> &sm) {
+    const int lane = threadIdx.x & 31;
+    for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
+    if (lane < NB / 32) sm.bits[lane] = 0;
+    if (lane == 0) sm.top = 0;
+    __syncwarp();
+    for (int i0 = 0; i0 < HC; i0 += 32) {
+        int i = i0 + lane;
+        int r = sm.val[i];
+        bool live = sm.key[i] != -1 && r != kDone;
+        pq_push(q, live, i, r < q.C ? r : q.C);
+    }
+}
+
+// One scan of Alg. 1 from `start` with id `sid` and key cap C.
+template <int HC, int NB>
+template <class Q>
+__device__ bool HashTable<HC, NB>::rebuild(Q &q) const {
+    pq_rebuild(q, *sm);
+    return true;
+}
+
+template <class Q>
+__device__ bool DenseTable::rebuild(Q &q) const {
+    const int lane = threadIdx.x & 31;
+    if (n_rebuild <= 0) return false;
+    for (int b = lane; b < Q::kNBuckets; b += 32) { q.head[b] = -1; q.tail[b] = -1; }
+    for (int b = lane; b < Q::kNBuckets / 32; b += 32) q.bits[b] = 0;
+    if (lane == 0) *q.top = 0;
+    __syncwarp();
+    for (int v0 = 0; v0 < n_rebuild; v0 += 32) {
+        const int v = v0 + lane;
+        const int rr = v < n_rebuild ? r[v] : 0;
+        const bool live = v < n_rebuild && rr > 0;  // kDone is negative
+        if (!pq_push(q, live, v, rr < q.C ? rr : q.C)) return false;
+    }
+    return true;
+}
+
+template <class Table, class Q>
+__device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt) {
+    const int lane = threadIdx.x & 31;
+    const int n = A.g.n;
+    const int C = q.C;
+    int *rv = tab.val();
+    {
+        int s = lane == 0 ? tab.find(start) : 0;
+        s = __shfl_sync(0xffffffffu, s, 0);
+        pq_push(q, lane == 0, s, 0);
+    }
+    long long alpha = 0, best = LLONG_MAX;
+    int nS = 0, best_len = 0;
+    bool alpha_ok = true, stop = false;
+    cnt.scans++;
+    while (!stop) {
+        int s = pq_pop(q, rv);
+        if (s < 0) break;
+        int x = tab.vertex(s);
+        int rx = rv[s];
+        __syncwarp();
+        int old = 0;
+        if (lane == 0) {
+            rv[s] = kDone;
+            old = atomicCAS(&A.T[x], 0, sid);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old != 0) {
+            cnt.black++;
+            continue;
+        }
+        long long L = 0, dx = 0;
+        int a0 = 0, a1 = 0;
+        if (lane == 0) {
+            A.order[x] = nS;
+            L = ld_volatile_i64(&A.st->lam);
+            a0 = A.g.rp[x];
+            a1 = A.g.rp[x + 1];
+            dx = A.g.deg[x];
+        }
+        L = __shfl_sync(0xffffffffu, L, 0);
+        dx = __shfl_sync(0xffffffffu, dx, 0);
+        a0 = __shfl_sync(0xffffffffu, a0, 0);
+        a1 = __shfl_sync(0xffffffffu, a1, 0);
+        ++nS;
+        if (rx >= kSat) alpha_ok = false;
+        alpha += dx - 2LL * rx;
+        if (alpha_ok && nS < n && alpha < L) {
+            if (lane == 0) atomicMin(&A.st->lam, alpha);
+            if (alpha < best) { best = alpha; best_len = nS; }
+            L = alpha;
+        }
+        cnt.verts++;
+        cnt.arcs += a1 - a0;
+        for (int i0 = a0; i0 < a1; i0 += 32) {
+            int i = i0 + lane;
+            bool v = i < a1;
+            int y = 0, c = 0;
+            if (v) {
+                int2 e = A.g.adj[i];
+                y = e.x;
+                c = e.y;
+            }
+            int s2 = v ? tab.find(y) : -1;
+            // a full table refuses new vertices: the arc stays unscanned (its
+            // weight is 0 in Lemma 1's lowered graph) and alpha is no longer
+            // the cut of S, but the scan goes on over the vertices it holds
+            if (__any_sync(0xffffffffu, v && s2 < 0)) alpha_ok = false;
+            bool push = false;
+            int kn = 0;
+            if (s2 >= 0) {
+                int r_old = rv[s2];
+                if (r_old != kDone) {
+                    int r_new = sat_add(r_old, c);
+                    rv[s2] = r_new;
+                    // a certificate q = min(r, C) can only vouch for bounds <= C
+                    if ((long long)r_old < L && L <= (long long)r_new && L <= (long long)C) {
+                        if (uf_union(A.par, x, y)) cnt.unions++;
+                    }
+                    int ko = r_old < C ? r_old : C;
+                    kn = r_new < C ? r_new : C;
+                    push = r_old == 0 || q.bucket(kn) != q.bucket(ko);
+                }
+            }
+            // a full pool is rebuilt from the live slots (they already hold
+            // this chunk's new keys); a table that cannot rebuild ends the scan
+            if (!pq_push(q, push, s2, kn) && !tab.rebuild(q)) {
+                stop = true;
+                alpha_ok = false;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        A.rec_alpha[sid] = best;
+        A.rec_len[sid] = best_len;
+    }
+}
+
+template <int HC_, int NB_>
+struct SmemQ : BucketQ<unsigned short, NB_> {
+    static constexpr int kHC = HC_;
+    static constexpr int kNB = NB_;
+};
+
+}  // namespace mc

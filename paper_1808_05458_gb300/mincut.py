@@ -63,7 +63,8 @@ _lib = None
 EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_graph_size",
            "mc_min_cut", "mc_batch_min_cut", "mc_strerror", "mc_graph_export",
            "mc_step_degrees", "mc_step_contract", "mc_step_pr", "mc_step_capforest",
-           "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc")
+           "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc",
+           "mc_batch_autotune")
 
 
 def library_path() -> str:
@@ -97,6 +98,7 @@ def load_library():
     lib.mc_step_capforest.argtypes = [vp, i64, P(McOptions), vp, P(i64), P(i64)]
     lib.mc_step_capforest_full.argtypes = [vp, i64, i32, vp, P(i64), P(i64)]
     lib.mc_step_label_prop.argtypes = [vp, i32, u64, vp]
+    lib.mc_batch_autotune.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), P(i32), vp, i32]
     lib.mc_capforest_full_noalloc.argtypes = [i32, i64, vp, vp, i64, i32, vp, P(i64), P(i64), vp]
     for f in EXPORTS:
         if f != "mc_strerror":
@@ -303,6 +305,24 @@ def min_cut(row_ptr, col, w, **opt) -> MinCut:
     """One-shot: create, solve, destroy."""
     with Graph(row_ptr, col, w) as g:
         return g.min_cut(options(**opt))
+
+
+def batch_autotune(row_ptr, col, w, vtx_off, arc_off, opts: McOptions | None = None):
+    """Pick the fastest batched-kernel shape for this batch (kept for later
+    batch_min_cut calls); returns (best shape index, per-shape kernel ms)."""
+    lib = load_library()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    ww = np.ascontiguousarray(w, dtype=np.int32)
+    vo = np.ascontiguousarray(vtx_off, dtype=np.int64)
+    ao = np.ascontiguousarray(arc_off, dtype=np.int64)
+    best = ctypes.c_int32()
+    ms = np.zeros(16, dtype=np.float64)
+    o = opts if opts is not None else options()
+    _check(lib.mc_batch_autotune(len(vo) - 1, _ptr(vo), _ptr(ao), _ptr(rp), _ptr(c), _ptr(ww),
+                                 ctypes.byref(o), ctypes.byref(best), _ptr(ms), 16),
+           "mc_batch_autotune")
+    return best.value, ms
 
 
 def batch_min_cut(row_ptr, col, w, vtx_off, arc_off, opts: McOptions | None = None,

@@ -285,12 +285,89 @@ def test_invalid_inputs(mc):
         mc.Graph(badrp, col, w)
 
 
+def _check_batch_sides(b, lam, bits, boff, ks):
+    for k in ks:
+        g = graphgen.batch_graph(b, k)
+        n = len(g[0]) - 1
+        side = np.unpackbits(bits[boff[k]:boff[k + 1]].view(np.uint8), bitorder="little")[:n]
+        assert side[0] == 0 and 0 < side.sum() < n
+        assert oracle.cut_weight(*g, side) == lam[k], k
+
+
 def test_batch_small(mc):
     b = graphgen.batch(7, G=48)
-    lam, _, _, _ = mc.batch_min_cut(*b)
+    lam, bits, boff, st = mc.batch_min_cut(*b, bitmaps=True)
     for k in range(48):
         g = graphgen.batch_graph(b, k)
         assert lam[k] == oracle.noi(*g)[0], k
+    _check_batch_sides(b, lam, bits, boff, range(48))
+
+
+def _concat(graphs):
+    rps, cols, ws, voff, aoff = [], [], [], [0], [0]
+    for rp, col, w in graphs:
+        rps.append(rp)
+        cols.append(col)
+        ws.append(w)
+        voff.append(voff[-1] + len(rp) - 1)
+        aoff.append(aoff[-1] + len(col))
+    return (np.concatenate(rps).astype(np.int32), np.concatenate(cols).astype(np.int32),
+            np.concatenate(ws).astype(np.int32), np.array(voff, dtype=np.int64),
+            np.array(aoff, dtype=np.int64))
+
+
+def test_batch_edge_cases(mc):
+    rng = np.random.default_rng(9)
+    graphs = [graphgen.from_edges(2, np.array([0]), np.array([1]), np.array([5])),
+              graphgen.from_edges(5, np.array([0, 1, 3]), np.array([1, 2, 4]), np.array([3, 3, 3])),
+              graphgen.cycle(40, 3), graphgen.complete(20, 2), graphgen.two_cliques(30, 4, seed=2),
+              graphgen.from_edges(4, np.array([0, 0, 1, 2, 3, 1]), np.array([1, 1, 2, 3, 3, 3]),
+                                  np.array([2, 3, 4, 5, 50, 0]))]
+    for i in range(40):
+        graphs.append(_random_tiny(rng, 1000 + i)[1])
+    graphs = [g for g in graphs if len(g[0]) - 1 >= 2]
+    b = _concat(graphs)
+    lam, bits, boff, _ = mc.batch_min_cut(*b, bitmaps=True)
+    for k, g in enumerate(graphs):
+        n = len(g[0]) - 1
+        ref = oracle.brute_force(*g)[0] if n <= 16 else oracle.stoer_wagner(*g)[0]
+        assert lam[k] == ref, (k, lam[k], ref)
+        side = np.unpackbits(bits[boff[k]:boff[k + 1]].view(np.uint8), bitorder="little")[:n]
+        assert side[0] == 0 and 0 < side.sum() < n and oracle.cut_weight(*g, side) == ref
+
+
+def test_batch_invalid(mc):
+    rp, col, w = graphgen.cycle(6)
+    bad = col.copy()
+    bad[3] = 17
+    b = _concat([(rp, bad, w)])
+    with pytest.raises(mc.MinCutError):
+        mc.batch_min_cut(*b)
+    b = _concat([(rp, col, -w)])
+    with pytest.raises(mc.MinCutError):
+        mc.batch_min_cut(*b)
+
+
+def test_batch_4096_full(mc):
+    # the batched workload: 4096 graphs, n in 50..2000, degree 4..16, weights 1..100
+    b = graphgen.batch(1)
+    lam, bits, boff, st = mc.batch_min_cut(*b, bitmaps=True)
+    ref = np.array([oracle.noi(*graphgen.batch_graph(b, k))[0] for k in range(4096)])
+    assert (lam == ref).all(), np.nonzero(lam != ref)[0][:10]
+    _check_batch_sides(b, lam, bits, boff, range(0, 4096, 7))
+    # Stoer-Wagner on a sample of the small graphs
+    small = [k for k in range(4096) if b[3][k + 1] - b[3][k] <= 150][:24]
+    for k in small:
+        assert lam[k] == oracle.stoer_wagner(*graphgen.batch_graph(b, k))[0]
+
+
+def test_batch_every_shape_and_autotune(mc):
+    b = graphgen.batch(3, G=256)
+    ref, _, _, _ = mc.batch_min_cut(*b)
+    best, ms = mc.batch_autotune(*b)
+    assert 0 <= best < 5 and (ms[:5] > 0).all()
+    lam, _, _, _ = mc.batch_min_cut(*b)
+    assert (lam == ref).all()
 
 
 # ------------------------------------------------------------ full sizes --
