@@ -147,6 +147,65 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
     return MC_OK;
 }
 
+// The bound phase: up to 8 levels of { LP sweeps -> contract the clusters ->
+// lambda-hat = min(., delta) -> PR tests -> contract }, then the exact loop on
+// what is left (at most kLpSmall vertices or no further clustering).  Runs on
+// Ga / Gb, leaves G0 untouched.
+template <class Exact>
+int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool verbose, i64 &bytes,
+             Exact exact) {
+    Work &w = g->w;
+    const int n0 = g->n0;
+    constexpr int kLpSmall = 2048;
+    const int iters = o.lp_iters > 0 ? o.lp_iters : 2;
+    DevGraph cur = g->G0;
+    DevGraph *nxt = &g->Ga;
+    for (int level = 0; level < 8 && cur.n > kLpSmall && lam > 0; ++level) {
+        MC_TRY(label_prop(cur, w, iters, o.seed ^ (0x9E37ULL * (u64)(level + 1)), w.lab, s));
+        bytes += (cur.arcs * 12 + (i64)cur.n * 12) * 2 * iters;
+        int nc = 0;
+        MC_TRY(compact_labels(w, cur.n, &nc, s));
+        if (verbose)
+            fprintf(stderr, "[mc] bound level %d: n=%d arcs=%lld -> %d clusters\n", level, cur.n,
+                    (long long)cur.arcs, nc);
+        if (nc < 2 || (long long)nc * 10 > (long long)cur.n * 9) break;
+        MC_TRY(round_reset(w, lam, s));
+        MC_TRY(contract_graph(cur, *nxt, w, lam, false, nc, s));
+        MC_TRY(orig_update(w, n0, s));
+        MC_TRY(min_degree(*nxt, w, s));
+        MC_TRY(status_read(w, s));
+        bytes += cur.arcs * 20;
+        if (w.h_st->mindeg < lam) {
+            lam = w.h_st->mindeg;
+            MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
+        }
+        cur = *nxt;
+        nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
+        // Padberg-Rinaldi on the cluster graph
+        MC_TRY(union_find_init(w.par, cur.n, s));
+        MC_TRY(round_reset(w, lam, s));
+        MC_TRY(pr_tests_budget(cur, w, lam, 1, 4, 64, s));
+        MC_TRY(status_read(w, s));
+        if (w.h_st->unions > 0 && cur.n >= 2) {
+            MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s));
+            MC_TRY(orig_update(w, n0, s));
+            MC_TRY(min_degree(*nxt, w, s));
+            MC_TRY(status_read(w, s));
+            if (nxt->n >= 2 && w.h_st->mindeg < lam) {
+                lam = w.h_st->mindeg;
+                MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
+            }
+            cur = *nxt;
+            nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
+        }
+        if (verbose)
+            fprintf(stderr, "[mc] bound level %d: after PR n=%d lam=%lld\n", level, cur.n, (long long)lam);
+    }
+    // the exact minimum cut of what is left is a cut of G as well
+    if (cur.n >= 2 && cur.rp != g->G0.rp) MC_TRY(exact(cur, nxt));
+    return MC_OK;
+}
+
 struct SolveOut {
     i64 lam = 0;
     mc_stats st{};
@@ -186,19 +245,20 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     MC_TRY(iota_i32(w.orig, n0, s));
     i64 lam = g->delta0;
     MC_TRY(side_from_vertex(w, n0, g->argmin0, s));
-    S.bound_initial = lam;
     bytes += g->G0.arcs * 8 + (i64)n0 * 12;  // degree sweep
-    S.ms_bound = ph.ms();
 
-    DevGraph cur = g->G0;
-    DevGraph *nxt = &g->Ga;
     ScanConfig cfg;
     cfg.pq_fifo = o.pq_order == MC_PQ_FIFO;
     cfg.warps = o.scans_per_round;
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
-    int rounds = 0, fallbacks = 0, guard = 0;
+    int rounds = 0, fallbacks = 0;
     const bool verbose = getenv("MC_VERBOSE") != nullptr;
+
+    // Alg. 2's loop from `cur`, contracting into the free buffer of Ga / Gb;
+    // lowers lam and records sides through w.orig
+    auto exact_loop = [&](DevGraph cur, DevGraph *nxt) -> int {
+    int guard = 0;
     while (cur.n >= 2 && lam > 0) {
         if (++guard > 4 * n0 + 64) return MC_EINTERNAL;
         cfg.round = rounds + guard;
@@ -301,6 +361,21 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
         ++rounds;
     }
+    return MC_OK;
+    };
+
+    // the label-propagation bound (VieCut, Sec. 2.3 / 3.1.1) on a contracted
+    // copy: every candidate is the weight of a real cut of G
+    if (o.bound == MC_BOUND_LP) {
+        MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); }));
+        MC_TRY(iota_i32(w.orig, n0, s));
+    }
+    S.bound_initial = lam;
+    S.ms_bound = ph.ms();
+    const int bound_rounds = rounds;
+    rounds = 0;
+    MC_TRY(exact_loop(g->G0, &g->Ga));
+    (void)bound_rounds;
     MC_TRY(side_canon(w, n0, s));
     S.rounds = rounds;
     S.fallback_rounds = fallbacks;
@@ -540,8 +615,11 @@ int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *lab
 
 int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *labels) {
     if (!g || !labels || iters < 0) return MC_EINVAL;
-    (void)seed;
-    return MC_EINVAL;
+    cudaStream_t s = g->stream;
+    MC_TRY(label_prop(g->G0, g->w, iters, seed, g->w.lab, s));
+    MC_CUDA(cudaMemcpyAsync(labels, g->w.lab, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
 }
 
 }  // extern "C"

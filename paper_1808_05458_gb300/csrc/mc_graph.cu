@@ -545,4 +545,28 @@ int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s) {
     return MC_OK;
 }
 
+__global__ void k_mark_used(const int *__restrict__ lab, int *used, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) used[v] = 0;
+}
+
+__global__ void k_mark_used2(const int *__restrict__ lab, int *used, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) used[lab[v]] = 1;
+}
+
+__global__ void k_apply_ids(int *lab, const int *__restrict__ ids, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) lab[v] = ids[lab[v]];
+}
+
+int compact_labels(Work &w, int n, int *nc, cudaStream_t s) {
+    ++::mc::g_launches; k_mark_used<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.root, n);
+    ++::mc::g_launches; k_mark_used2<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.root, n);
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    MC_TRY(exclusive_scan_i32(w.root, w.par, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
+    ++::mc::g_launches; k_apply_ids<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.par, n);
+    MC_CUDA(cudaGetLastError());
+    MC_TRY(status_read(w, s));
+    *nc = (int)w.h_st->count;
+    return MC_OK;
+}
+
 }  // namespace mc

@@ -216,8 +216,12 @@ int batch_shapes();
 void batch_set_shape(int shape);
 int batch_get_shape();
 
-// label propagation sweeps on g into labels (int32[n])
+// label propagation sweeps on g into labels (int32[n]; uses w.cnt, w.T and
+// the radix buffers as scratch)
 int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cudaStream_t s);
+// labels in w.lab (arbitrary vertex ids) -> dense ids in [0, nc) by the order
+// of the label values; uses w.root / w.par as scratch
+int compact_labels(Work &w, int n, int *nc, cudaStream_t s);
 
 // ---------------------------------------------------------- device bits --
 __device__ __forceinline__ u64 splitmix64(u64 x) {

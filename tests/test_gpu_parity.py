@@ -431,3 +431,46 @@ def test_full_scan_deterministic_on_ties(mc):
             assert_root_labels(lab)
         for lab, lo, un in runs[1:]:
             assert (lab == runs[0][0]).all() and lo == runs[0][1] and un == runs[0][2]
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_label_prop_parity(mc, iters):
+    # bit-exact against the oracle's reading of label propagation, on rows
+    # short (registers), medium (shared-memory hash) and long (hub kernel)
+    graphs = [graphgen.random_connected(500, 3000, seed=11, wmax=7),
+              graphgen.planted(4, block_n=400, avg_deg=16, cross=6),
+              graphgen.rhg(2, 1 << 14, 24.0),
+              graphgen.rmat_kcore(2, scale=14, k=6)]
+    # a star with a 3000-arc hub plus a ring, weights 1..9
+    rng = np.random.default_rng(5)
+    hub_u = np.zeros(3000, dtype=np.int64)
+    hub_v = np.arange(1, 3001)
+    ring_u = np.arange(1, 3001)
+    ring_v = np.roll(ring_u, 1)
+    u = np.concatenate([hub_u, ring_u])
+    v = np.concatenate([hub_v, ring_v])
+    graphs.append(graphgen.from_edges(3001, u, v, rng.integers(1, 10, size=len(u))))
+    for k, g in enumerate(graphs):
+        with mc.Graph(*g) as G:
+            lab = G.label_prop(iters, seed=77 + k)
+        assert (lab == oracle.label_prop(*g, iters, 77 + k)).all(), k
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_lp_bound_planted(mc, seed):
+    # the LP bound keeps lambda exact and finds the planted cut
+    g = graphgen.planted(seed)
+    ref, _, _ = oracle.noi(*g)
+    with mc.Graph(*g) as G:
+        res = G.min_cut(mc.options(bound=mc.MC_BOUND_LP))
+    check_cut(mc, g, res, ref)
+    assert res.stats["bound_initial"] >= ref
+
+
+def test_lp_bound_lambda_unchanged(mc):
+    for g in (graphgen.rhg(3, 1 << 16, 32.0), graphgen.rmat_kcore(3, scale=16),
+              graphgen.random_connected(4000, 30000, seed=3, wmax=20)):
+        ref, _, _ = oracle.noi(*g)
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(bound=mc.MC_BOUND_LP, lp_iters=3))
+        check_cut(mc, g, res, ref)
