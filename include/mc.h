@@ -59,6 +59,8 @@ extern "C" {
 
 #define MC_BOUND_DEGREE 0  /* lambda-hat = minimum weighted degree            */
 #define MC_BOUND_LP 1      /* + label-propagation clustering bound (VieCut)   */
+#define MC_BOUND_LEARNED 2 /* + the learned proposer's sweep cut (opt.proposer) */
+#define MC_BOUND_BEST 3    /* + both                                          */
 
 typedef struct mc_options {
     int32_t pq_order;        /* MC_PQ_LIFO (default) or MC_PQ_FIFO             */
@@ -71,6 +73,7 @@ typedef struct mc_options {
     int32_t lp_iters;        /* label-propagation sweeps for MC_BOUND_LP, 0=auto*/
     uint64_t seed;           /* start vertices / LP parity                      */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = the graph's own */
+    void *proposer;          /* mc_proposer* for MC_BOUND_LEARNED / _BEST      */
 } mc_options;
 
 /* Per-call statistics (all optional). */
@@ -183,6 +186,33 @@ int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
 
 /* Message for an error code (thread-local detail for MC_ECUDA). */
 const char *mc_strerror(int code);
+
+/* ---- learned bound proposer -----------------------------------------------
+ * A 3-layer message-passing network (hidden 64, BF16 activations, FP32
+ * sums, tensor-core dense transforms) scores every vertex; the best sweep
+ * cut over the scores is an exact integer cut of G and therefore an upper
+ * bound on lambda.  mc_min_cut uses it only if it is below the bound it
+ * already has, so lambda never depends on the network.  The paper has no
+ * learned component.  Parameters are MC_PROPOSER_PARAMS floats (layout in
+ * mc_learn.cu).  Graph arguments are graphs made by mc_graph_create; host
+ * arrays unless stated.                                                     */
+#define MC_PROPOSER_PARAMS 25409
+typedef struct mc_proposer mc_proposer;
+/* params: NULL = Glorot-uniform init from `seed` (biases 0). */
+int mc_proposer_create(const float *params, uint64_t seed, mc_proposer **out);
+int mc_proposer_destroy(mc_proposer *p);
+int mc_proposer_get(mc_proposer *p, float *params);
+int mc_proposer_set(mc_proposer *p, const float *params);
+/* logits (n floats) of the forward pass on g */
+int mc_proposer_forward(mc_proposer *p, mc_graph *g, float *logits);
+/* polarity-invariant BCE loss of the side bitmap (ceil(n/32) words) and its
+ * gradient (MC_PROPOSER_PARAMS floats, may be NULL) */
+int mc_proposer_grad(mc_proposer *p, mc_graph *g, const uint32_t *side, double *loss, float *grad);
+/* forward + backward + one Adam step (beta 0.9 / 0.999) at learning rate lr */
+int mc_proposer_train_step(mc_proposer *p, mc_graph *g, const uint32_t *side, float lr, double *loss);
+/* the best sweep cut over the scores: *cut (exact) and its side (bitmap,
+ * canonical polarity, may be NULL) */
+int mc_proposer_bound(mc_proposer *p, mc_graph *g, int64_t *cut, uint32_t *side);
 
 /* ---- step-level entry points (same kernels as mc_min_cut) ---------------
  * These expose single steps of the path on a created graph for parity

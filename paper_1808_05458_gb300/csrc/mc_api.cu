@@ -7,6 +7,7 @@
 // Every improvement of lambda-hat snapshots its side as a bitmap over the
 // original vertices (Sec. 3.3): a scan's prefix for an alpha cut, the
 // preimage of a contracted vertex for a degree cut.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -366,9 +367,22 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
 
     // the label-propagation bound (VieCut, Sec. 2.3 / 3.1.1) on a contracted
     // copy: every candidate is the weight of a real cut of G
-    if (o.bound == MC_BOUND_LP) {
+    if (o.bound == MC_BOUND_LP || o.bound == MC_BOUND_BEST) {
         MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); }));
         MC_TRY(iota_i32(w.orig, n0, s));
+    }
+    // the learned proposer's sweep cut (used only when it is lower)
+    if ((o.bound == MC_BOUND_LEARNED || o.bound == MC_BOUND_BEST) && o.proposer) {
+        Proposer *pp = reinterpret_cast<Proposer *>(o.proposer);
+        long long cut = 0;
+        int k = 0;
+        MC_TRY(proposer_forward(*pp, g->G0, g->delta0, s));
+        MC_TRY(proposer_sweep(*pp, g->G0, w, &cut, &k, s));
+        if (verbose) fprintf(stderr, "[mc] proposer sweep cut %lld (k=%d), bound %lld\n", cut, k, (long long)lam);
+        if (cut < lam) {
+            lam = cut;
+            MC_TRY(side_from_rank(w, n0, k, s));
+        }
     }
     S.bound_initial = lam;
     S.ms_bound = ph.ms();
@@ -492,6 +506,106 @@ int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
     }
     batch_set_shape(best);
     if (best_shape) *best_shape = best;
+    return MC_OK;
+}
+
+int mc_proposer_create(const float *params, uint64_t seed, mc_proposer **out) {
+    if (!out) return MC_EINVAL;
+    const int P = proposer_nparams();
+    std::vector<float> init((size_t)P, 0.f);
+    if (params) {
+        memcpy(init.data(), params, sizeof(float) * (size_t)P);
+    } else {
+        // Glorot-uniform weights, zero biases (layout in mc_learn.cu)
+        u64 st = seed ^ 0x2545F4914F6CDD1DULL;
+        auto uni = [&]() {
+            st += 0x9E3779B97F4A7C15ULL;
+            u64 z = st;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+            z ^= z >> 31;
+            return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        };
+        auto fill = [&](int off, int fan_in, int fan_out) {
+            const double a = std::sqrt(6.0 / (fan_in + fan_out));
+            for (int i = 0; i < fan_in * fan_out; ++i) init[(size_t)off + i] = (float)((2 * uni() - 1) * a);
+        };
+        fill(0, 8, 64);
+        for (int l = 0; l < 3; ++l) fill(8 * 64 + 64 + l * (128 * 64 + 64), 128, 64);
+        fill(8 * 64 + 64 + 3 * (128 * 64 + 64), 64, 1);
+    }
+    Proposer *p = nullptr;
+    MC_TRY(proposer_create(&p, init.data()));
+    *out = reinterpret_cast<mc_proposer *>(p);
+    return MC_OK;
+}
+
+int mc_proposer_destroy(mc_proposer *p) {
+    if (!p) return MC_EINVAL;
+    proposer_destroy(reinterpret_cast<Proposer *>(p));
+    return MC_OK;
+}
+
+int mc_proposer_get(mc_proposer *p, float *params) {
+    if (!p || !params) return MC_EINVAL;
+    return proposer_get(reinterpret_cast<Proposer *>(p), params);
+}
+
+int mc_proposer_set(mc_proposer *p, const float *params) {
+    if (!p || !params) return MC_EINVAL;
+    return proposer_set(reinterpret_cast<Proposer *>(p), params);
+}
+
+int mc_proposer_forward(mc_proposer *p, mc_graph *g, float *logits) {
+    if (!p || !g || !logits) return MC_EINVAL;
+    Proposer &pp = *reinterpret_cast<Proposer *>(p);
+    MC_TRY(proposer_forward(pp, g->G0, g->delta0, g->stream));
+    MC_CUDA(cudaStreamSynchronize(g->stream));
+    return proposer_logits_copy(pp, g->n0, logits);
+}
+
+static int upload_side(mc_graph *g, const uint32_t *side) {
+    MC_CUDA(cudaMemcpyAsync(g->w.best_side, side, sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32),
+                            cudaMemcpyHostToDevice, g->stream));
+    return MC_OK;
+}
+
+int mc_proposer_grad(mc_proposer *p, mc_graph *g, const uint32_t *side, double *loss, float *grad) {
+    if (!p || !g || !side || !loss) return MC_EINVAL;
+    Proposer &pp = *reinterpret_cast<Proposer *>(p);
+    MC_TRY(upload_side(g, side));
+    MC_TRY(proposer_forward(pp, g->G0, g->delta0, g->stream));
+    MC_TRY(proposer_backward(pp, g->G0, g->w.best_side, loss, g->stream));
+    if (grad) MC_TRY(proposer_grad_copy(pp, grad));
+    return MC_OK;
+}
+
+int mc_proposer_train_step(mc_proposer *p, mc_graph *g, const uint32_t *side, float lr, double *loss) {
+    if (!p || !g || !side || !loss || !(lr > 0)) return MC_EINVAL;
+    Proposer &pp = *reinterpret_cast<Proposer *>(p);
+    MC_TRY(upload_side(g, side));
+    MC_TRY(proposer_forward(pp, g->G0, g->delta0, g->stream));
+    MC_TRY(proposer_backward(pp, g->G0, g->w.best_side, loss, g->stream));
+    MC_TRY(proposer_adam(pp, lr, g->stream));
+    MC_CUDA(cudaStreamSynchronize(g->stream));
+    return MC_OK;
+}
+
+int mc_proposer_bound(mc_proposer *p, mc_graph *g, int64_t *cut, uint32_t *side) {
+    if (!p || !g || !cut) return MC_EINVAL;
+    Proposer &pp = *reinterpret_cast<Proposer *>(p);
+    long long c = 0;
+    int k = 0;
+    MC_TRY(proposer_forward(pp, g->G0, g->delta0, g->stream));
+    MC_TRY(proposer_sweep(pp, g->G0, g->w, &c, &k, g->stream));
+    *cut = c;
+    if (side) {
+        MC_TRY(side_from_rank(g->w, g->n0, k, g->stream));
+        MC_TRY(side_canon(g->w, g->n0, g->stream));
+        MC_CUDA(cudaMemcpyAsync(side, g->w.best_side, sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32),
+                                cudaMemcpyDeviceToHost, g->stream));
+    }
+    MC_CUDA(cudaStreamSynchronize(g->stream));
     return MC_OK;
 }
 

@@ -569,4 +569,16 @@ int compact_labels(Work &w, int n, int *nc, cudaStream_t s) {
     return MC_OK;
 }
 
+struct SideRank {
+    const int *rank;
+    int k;
+    __device__ bool operator()(int v) const { return rank[v] < k; }
+};
+
+int side_from_rank(Work &w, int n0, int k, cudaStream_t s) {
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideRank{w.root, k});
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 }  // namespace mc

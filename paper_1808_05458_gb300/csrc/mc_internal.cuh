@@ -216,6 +216,21 @@ int batch_shapes();
 void batch_set_shape(int shape);
 int batch_get_shape();
 
+// learned proposer (mc_learn.cu)
+struct Proposer;
+int proposer_create(Proposer **out, const float *init);
+void proposer_destroy(Proposer *p);
+int proposer_set(Proposer *p, const float *w);
+int proposer_get(Proposer *p, float *w);
+int proposer_nparams();
+int proposer_forward(Proposer &p, const DevGraph &g, long long delta, cudaStream_t s);
+int proposer_backward(Proposer &p, const DevGraph &g, const unsigned *bits, double *loss, cudaStream_t s);
+int proposer_adam(Proposer &p, float lr, cudaStream_t s);
+int proposer_grad_copy(Proposer &p, float *out);
+int proposer_logits_copy(Proposer &p, int n, float *out);
+int proposer_sweep(Proposer &p, const DevGraph &g, Work &w, long long *cut, int *k_out, cudaStream_t s);
+int side_from_rank(Work &w, int n0, int k, cudaStream_t s);  // bit v = w.root[v] < k
+
 // label propagation sweeps on g into labels (int32[n]; uses w.cnt, w.T and
 // the radix buffers as scratch)
 int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cudaStream_t s);

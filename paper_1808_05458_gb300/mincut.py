@@ -29,13 +29,17 @@ MC_PQ_LIFO = 0
 MC_PQ_FIFO = 1
 MC_BOUND_DEGREE = 0
 MC_BOUND_LP = 1
+MC_BOUND_LEARNED = 2
+MC_BOUND_BEST = 3
+PROPOSER_PARAMS = 25409
 
 
 class McOptions(ctypes.Structure):
     _fields_ = [("pq_order", ctypes.c_int32), ("bound", ctypes.c_int32),
                 ("pr_level", ctypes.c_int32), ("scans_per_round", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("lp_iters", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+                ("proposer", ctypes.c_void_p)]
 
 
 class McStats(ctypes.Structure):
@@ -64,7 +68,9 @@ EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_grap
            "mc_min_cut", "mc_batch_min_cut", "mc_strerror", "mc_graph_export",
            "mc_step_degrees", "mc_step_contract", "mc_step_pr", "mc_step_capforest",
            "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc",
-           "mc_batch_autotune")
+           "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
+           "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
+           "mc_proposer_bound")
 
 
 def library_path() -> str:
@@ -98,6 +104,16 @@ def load_library():
     lib.mc_step_capforest.argtypes = [vp, i64, P(McOptions), vp, P(i64), P(i64)]
     lib.mc_step_capforest_full.argtypes = [vp, i64, i32, vp, P(i64), P(i64)]
     lib.mc_step_label_prop.argtypes = [vp, i32, u64, vp]
+    F32P = P(ctypes.c_float)
+    lib.mc_proposer_create.argtypes = [vp, u64, P(vp)]
+    lib.mc_proposer_destroy.argtypes = [vp]
+    lib.mc_proposer_get.argtypes = [vp, vp]
+    lib.mc_proposer_set.argtypes = [vp, vp]
+    lib.mc_proposer_forward.argtypes = [vp, vp, vp]
+    lib.mc_proposer_grad.argtypes = [vp, vp, vp, P(ctypes.c_double), vp]
+    lib.mc_proposer_train_step.argtypes = [vp, vp, vp, ctypes.c_float, P(ctypes.c_double)]
+    lib.mc_proposer_bound.argtypes = [vp, vp, P(i64), vp]
+    del F32P
     lib.mc_batch_autotune.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), P(i32), vp, i32]
     lib.mc_capforest_full_noalloc.argtypes = [i32, i64, vp, vp, i64, i32, vp, P(i64), P(i64), vp]
     for f in EXPORTS:
@@ -301,6 +317,94 @@ def capforest_full_noalloc(row_ptr, adj, lam: int, start: int, labels, stream=No
     return lo.value, un.value
 
 
+class Proposer:
+    """The learned bound proposer (``mc_proposer``): a 3-layer message-passing
+    network whose best sweep cut is an exact upper bound on lambda."""
+
+    MAGIC = b"MCPROP01"
+
+    def __init__(self, params=None, seed: int = 0):
+        lib = load_library()
+        self._h = ctypes.c_void_p()
+        arr = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            assert arr.size == PROPOSER_PARAMS
+        _check(lib.mc_proposer_create(_ptr(arr), ctypes.c_uint64(seed & (2**64 - 1)),
+                                      ctypes.byref(self._h)), "mc_proposer_create")
+
+    def close(self):
+        if self._h:
+            load_library().mc_proposer_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def get(self) -> np.ndarray:
+        out = np.zeros(PROPOSER_PARAMS, dtype=np.float32)
+        _check(load_library().mc_proposer_get(self._h, _ptr(out)), "mc_proposer_get")
+        return out
+
+    def set(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load_library().mc_proposer_set(self._h, _ptr(arr)), "mc_proposer_set")
+
+    def forward(self, g: "Graph") -> np.ndarray:
+        out = np.zeros(g.n, dtype=np.float32)
+        _check(load_library().mc_proposer_forward(self._h, g._h, _ptr(out)), "mc_proposer_forward")
+        return out
+
+    def grad(self, g: "Graph", side_bits):
+        bits = np.ascontiguousarray(side_bits, dtype=np.uint32)
+        loss = ctypes.c_double()
+        grad = np.zeros(PROPOSER_PARAMS, dtype=np.float32)
+        _check(load_library().mc_proposer_grad(self._h, g._h, _ptr(bits), ctypes.byref(loss),
+                                               _ptr(grad)), "mc_proposer_grad")
+        return loss.value, grad
+
+    def train_step(self, g: "Graph", side_bits, lr: float) -> float:
+        bits = np.ascontiguousarray(side_bits, dtype=np.uint32)
+        loss = ctypes.c_double()
+        _check(load_library().mc_proposer_train_step(self._h, g._h, _ptr(bits), ctypes.c_float(lr),
+                                                     ctypes.byref(loss)), "mc_proposer_train_step")
+        return loss.value
+
+    def bound(self, g: "Graph"):
+        cut = ctypes.c_int64()
+        side = np.zeros((g.n + 31) // 32, dtype=np.uint32)
+        _check(load_library().mc_proposer_bound(self._h, g._h, ctypes.byref(cut), _ptr(side)),
+               "mc_proposer_bound")
+        return cut.value, side
+
+    # versioned weight blob: magic, count (uint32), float32 params, sha256
+    def save(self, path: str):
+        import hashlib
+        w = self.get().astype("<f4").tobytes()
+        body = self.MAGIC + np.uint32(PROPOSER_PARAMS).tobytes() + w
+        with open(path, "wb") as f:
+            f.write(body + hashlib.sha256(body).digest())
+
+    @classmethod
+    def load(cls, path: str) -> "Proposer":
+        import hashlib
+        data = open(path, "rb").read()
+        body, digest = data[:-32], data[-32:]
+        if body[:8] != cls.MAGIC or hashlib.sha256(body).digest() != digest:
+            raise ValueError(f"{path}: not a proposer weight file or corrupted")
+        count = int(np.frombuffer(body[8:12], dtype="<u4")[0])
+        if count != PROPOSER_PARAMS:
+            raise ValueError(f"{path}: {count} parameters, expected {PROPOSER_PARAMS}")
+        return cls(np.frombuffer(body[12:], dtype="<f4").copy())
+
+
 def min_cut(row_ptr, col, w, **opt) -> MinCut:
     """One-shot: create, solve, destroy."""
     with Graph(row_ptr, col, w) as g:
@@ -321,7 +425,9 @@ def batch_autotune(row_ptr, col, w, vtx_off, arc_off, opts: McOptions | None = N
     o = opts if opts is not None else options()
     _check(lib.mc_batch_autotune(len(vo) - 1, _ptr(vo), _ptr(ao), _ptr(rp), _ptr(c), _ptr(ww),
                                  ctypes.byref(o), ctypes.byref(best), _ptr(ms), 16),
-           "mc_batch_autotune")
+           "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
+           "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
+           "mc_proposer_bound")
     return best.value, ms
 
 

@@ -1,0 +1,142 @@
+"""The learned bound proposer on the GPU against its FP64 reference.
+
+* forward logits and the full parameter gradient (BF16 activations, FP32
+  sums on the tensor cores) against oracle/gnn.py in float64;
+* the proposed bound is an exact cut: its weight re-computed by the oracle,
+  and equal to the best prefix cut of the score order computed on the host;
+* lambda never changes when the proposer supplies the bound;
+* training on the GPU lowers the loss, and weights survive save / load.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(os.path.dirname(HERE), "paper_1808_05458_gb300", "weights",
+                       "proposer_rhg16_d64.bin")
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1808_05458_gb300 as m
+    m.load_library()
+    return m
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _graphs():
+    return [graphgen.random_connected(300, 1500, seed=31, wmax=9),
+            graphgen.planted(5, block_n=200, avg_deg=12, cross=4),
+            graphgen.rhg(9, 1 << 11, 24.0)]
+
+
+def test_forward_and_gradient_match_fp64(mc):
+    from oracle import gnn
+    rng = np.random.default_rng(2)
+    for t, g in enumerate(_graphs()):
+        n = len(g[0]) - 1
+        params = gnn.glorot(10 + t)
+        side = (rng.random(n) < 0.4).astype(np.uint8)
+        bits = np.packbits(side, bitorder="little").view(np.uint8)
+        bits = np.concatenate([bits, np.zeros((-len(bits)) % 4, np.uint8)]).view(np.uint32)
+        P = mc.Proposer(params.astype(np.float32))
+        with mc.Graph(*g) as G:
+            logits = P.forward(G)
+            loss, grad = P.grad(G, bits)
+        ref_s, _ = gnn.forward(params, *g)
+        ref_loss, ref_grad = gnn.loss_and_grad(params, *g, side.astype(np.int64))
+        assert _rel(logits, ref_s) < 2e-2, (t, _rel(logits, ref_s))
+        assert abs(loss - ref_loss) < 2e-2 * abs(ref_loss)
+        assert _rel(grad, ref_grad) < 3e-2, (t, _rel(grad, ref_grad))
+        # every parameter block individually
+        blocks = [(gnn.P_WIN, gnn.P_BIN), (gnn.P_BIN, gnn.P_W0)] + \
+                 [(gnn.P_W0 + l * gnn.P_LAYER, gnn.P_W0 + (l + 1) * gnn.P_LAYER) for l in range(3)] + \
+                 [(gnn.P_WOUT, gnn.P_TOTAL)]
+        for a, b in blocks:
+            if np.linalg.norm(ref_grad[a:b]) > 1e-6:
+                assert _rel(grad[a:b], ref_grad[a:b]) < 5e-2, (t, a, _rel(grad[a:b], ref_grad[a:b]))
+        P.close()
+
+
+def test_sweep_bound_is_an_exact_cut(mc):
+    for t, g in enumerate(_graphs() + [graphgen.rhg(3, 1 << 14, 32.0)]):
+        n = len(g[0]) - 1
+        P = mc.Proposer(seed=t)
+        with mc.Graph(*g) as G:
+            logits = P.forward(G)
+            cut, bits = P.bound(G)
+            res = G.min_cut()
+        side = mc.bitmap_to_side(bits, n)
+        assert side[0] == 0 and 0 < side.sum() < n
+        assert oracle.cut_weight(*g, side) == cut
+        assert cut >= res.lam
+        # best prefix cut of the (score, vertex) order, on the host
+        order = np.lexsort((np.arange(n), logits))
+        best = min(oracle.cut_weight(*g, np.isin(np.arange(n), order[:k]).astype(np.uint8))
+                   for k in range(1, n)) if n <= 400 else cut
+        assert cut == best
+        P.close()
+
+
+def test_lambda_unchanged_with_the_proposer(mc):
+    P = mc.Proposer(seed=5)
+    for g in (graphgen.planted(2), graphgen.rhg(5, 1 << 15, 32.0),
+              graphgen.random_connected(2000, 9000, seed=4, wmax=30)):
+        ref, _, _ = oracle.noi(*g)
+        for bound in (mc.MC_BOUND_LEARNED, mc.MC_BOUND_BEST):
+            with mc.Graph(*g) as G:
+                res = G.min_cut(mc.options(bound=bound, proposer=P.handle))
+            side = res.side(len(g[0]) - 1)
+            assert res.lam == ref and oracle.cut_weight(*g, side) == ref
+    P.close()
+
+
+def test_training_lowers_loss_and_save_load(mc, tmp_path):
+    g = graphgen.planted(7, block_n=300, avg_deg=14, cross=5)
+    n = len(g[0]) - 1
+    side = np.zeros(n, dtype=np.uint8)
+    side[300:] = 1
+    bits = np.packbits(side, bitorder="little")
+    bits = np.concatenate([bits, np.zeros((-len(bits)) % 4, np.uint8)]).view(np.uint32)
+    P = mc.Proposer(seed=1)
+    with mc.Graph(*g) as G:
+        first = P.train_step(G, bits, 3e-3)
+        for _ in range(60):
+            last = P.train_step(G, bits, 3e-3)
+    assert last < first
+    path = str(tmp_path / "w.bin")
+    P.save(path)
+    Q = mc.Proposer.load(path)
+    assert (Q.get() == P.get()).all()
+    P.close()
+    Q.close()
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights committed")
+def test_trained_weights_gain_report(mc):
+    # what the trained network gains over the method without it, on held-out
+    # graphs of the training family: its loss against the solver's sides is
+    # below an untrained network's, and its bound never goes below lambda
+    T = mc.Proposer.load(WEIGHTS)
+    U = mc.Proposer(seed=123)
+    lt, lu = [], []
+    for seed in (900, 901):
+        g = graphgen.rhg(seed, 1 << 16, 64.0)
+        with mc.Graph(*g) as G:
+            res = G.min_cut()
+            lt.append(T.grad(G, res.bitmap)[0])
+            lu.append(U.grad(G, res.bitmap)[0])
+            cut, _ = T.bound(G)
+            assert cut >= res.lam
+    assert np.mean(lt) < np.mean(lu)

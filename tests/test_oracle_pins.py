@@ -384,3 +384,30 @@ def test_pr_degree2_tie_rule_cycle_and_chain():
     roots, lab2 = np.unique(lab, return_inverse=True)
     crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
     assert oracle.stoer_wagner(crp.astype(np.int32), ccol, cw.astype(np.int32))[0] == 1
+
+
+def test_gnn_reference_gradient_matches_finite_differences():
+    # the FP64 reference network's analytic backward pass against central
+    # differences of its own loss, on small random graphs
+    from oracle import gnn
+    rng = np.random.default_rng(17)
+    for t in range(3):
+        g = graphgen.random_connected(30 + 10 * t, 60, seed=200 + t, wmax=9)
+        n = len(g[0]) - 1
+        side = (rng.random(n) < 0.3).astype(np.int64)
+        params = gnn.glorot(t)
+        loss, grad = gnn.loss_and_grad(params, *g, side)
+        assert abs(loss - gnn.loss_only(params, *g, side)) < 1e-12
+        idx = np.concatenate([rng.choice(gnn.P_TOTAL, 40, replace=False),
+                              [gnn.P_BOUT, gnn.P_BIN, gnn.P_W0 + 5, gnn.P_W0 + 64 * 64 + 3]])
+        num = gnn.numeric_grad(params, *g, side, idx)
+        assert np.allclose(grad[idx], num, rtol=1e-4, atol=1e-8), (t, np.max(np.abs(grad[idx] - num)))
+
+
+def test_gnn_reference_polarity_invariant():
+    from oracle import gnn
+    g = graphgen.random_connected(25, 50, seed=9, wmax=5)
+    n = len(g[0]) - 1
+    side = (np.arange(n) % 3 == 0).astype(np.int64)
+    p = gnn.glorot(4)
+    assert gnn.loss_only(p, *g, side) == gnn.loss_only(p, *g, 1 - side)
