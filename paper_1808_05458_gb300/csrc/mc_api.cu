@@ -275,6 +275,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         auto scan_round = [&](int budget, i64 *unions_out) -> int {
             ScanConfig c2 = cfg;
             c2.budget = budget;
+            c2.lam_hint = lam;
             MC_CUDA(cudaEventRecord(ka, s));
             MC_TRY(capforest_parallel(cur, w, c2, s));
             MC_CUDA(cudaEventRecord(kb, s));
@@ -697,6 +698,7 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     cfg.warps = o.scans_per_round;
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
+    cfg.lam_hint = lam;
     MC_TRY(union_find_init(g->w.par, g->n0, s));
     MC_TRY(round_reset(g->w, lam, s));
     MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));

@@ -36,23 +36,13 @@
 
 namespace mc {
 
-template <int WPB, int HC, int NB>
-__global__ void __launch_bounds__(WPB * 32)
-k_capforest(ScanArgs A, int fifo) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// Start vertices come from a shared cursor over a pseudo-random permutation
+// of the vertices (an affine map with a stride coprime to n); each warp takes
+// 32 at a time and scans the ones no scan owns yet.  scan(start, sid, L) runs
+// one scan with cap L.
+template <class ScanFn>
+__device__ void scan_driver(const ScanArgs &A, Counters &cnt, ScanFn scan) {
     const int lane = threadIdx.x & 31;
-    ScanSmem<HC, NB> &sm = reinterpret_cast<ScanSmem<HC, NB> *>(smem_raw)[threadIdx.x >> 5];
-    HashTable<HC, NB> tab{&sm, A.limit};
-    SmemQ<HC, NB> q;
-    q.head = sm.head;
-    q.tail = sm.tail;
-    q.bits = sm.bits;
-    q.eslot = sm.eslot;
-    q.enext = sm.enext;
-    q.top = &sm.top;
-    q.cap = 2 * HC;
-    q.fifo = fifo != 0;
-    Counters cnt;
     const u64 n = (u64)A.g.n;
     while (true) {
         u64 base = 0;
@@ -83,15 +73,7 @@ k_capforest(ScanArgs A, int fifo) {
             int sid = 0;
             if (lane == 0) sid = atomicAdd(&A.st->scan_ids, 1) + 1;
             sid = __shfl_sync(0xffffffffu, sid, 0);
-            // reset the warp's table and queue
-            for (int i = lane; i < HC; i += 32) sm.key[i] = -1;
-            for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
-            if (lane < NB / 32) sm.bits[lane] = 0;
-            if (lane == 0) { sm.top = 0; sm.used = 0; }
-            __syncwarp();
-            q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
-            q.coarse = q.C + 1 > NB;
-            scan_one<HashTable<HC, NB>, SmemQ<HC, NB>>(A, tab, q, start, sid, cnt);
+            scan(start, sid, L);
         }
     }
     // flush counters: unions are per lane, the rest are warp-uniform
@@ -105,6 +87,60 @@ k_capforest(ScanArgs A, int fifo) {
         atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->blacklisted), (unsigned long long)cnt.black);
         atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), (unsigned long long)cnt.scans);
     }
+}
+
+// concurrent scans with the list bucket queue (any cap)
+template <int WPB, int HC, int NB>
+__global__ void __launch_bounds__(WPB * 32)
+k_capforest(ScanArgs A, int fifo) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    ScanSmem<HC, NB> &sm = reinterpret_cast<ScanSmem<HC, NB> *>(smem_raw)[threadIdx.x >> 5];
+    HashTable<HC, ScanSmem<HC, NB>> tab{&sm, A.limit};
+    SmemQ<HC, NB> q;
+    q.head = sm.head;
+    q.tail = sm.tail;
+    q.bits = sm.bits;
+    q.eslot = sm.eslot;
+    q.enext = sm.enext;
+    q.top = &sm.top;
+    q.cap = 2 * HC;
+    q.fifo = fifo != 0;
+    Counters cnt;
+    scan_driver(A, cnt, [&](int start, int sid, long long L) {
+        for (int i = lane; i < HC; i += 32) sm.key[i] = -1;
+        for (int b = lane; b < NB; b += 32) { sm.head[b] = -1; sm.tail[b] = -1; }
+        if (lane < NB / 32) sm.bits[lane] = 0;
+        if (lane == 0) { sm.top = 0; sm.used = 0; }
+        __syncwarp();
+        q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
+        q.coarse = q.C + 1 > NB;
+        scan_one<HashTable<HC, ScanSmem<HC, NB>>, SmemQ<HC, NB>, true>(A, tab, q, start, sid, cnt);
+    });
+}
+
+// concurrent scans with the bitmap bucket queue (cap < NBK at launch; the
+// cap only falls during the launch)
+template <int WPB, int HC, int NBK>
+__global__ void __launch_bounds__(WPB * 32)
+k_capforest_bit(ScanArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    ScanSmemBit<HC, NBK> &sm = reinterpret_cast<ScanSmemBit<HC, NBK> *>(smem_raw)[threadIdx.x >> 5];
+    HashTable<HC, ScanSmemBit<HC, NBK>> tab{&sm, A.limit};
+    BitQ<HC, NBK> q;
+    q.bits = sm.bits;
+    q.cnt = sm.cnt;
+    Counters cnt;
+    scan_driver(A, cnt, [&](int start, int sid, long long L) {
+        for (int i = lane; i < HC; i += 32) sm.key[i] = -1;
+        for (int i = lane; i < NBK * (HC / 32); i += 32) sm.bits[i] = 0;
+        for (int i = lane; i < NBK; i += 32) sm.cnt[i] = 0;
+        if (lane == 0) sm.used = 0;
+        __syncwarp();
+        q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
+        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, true>(A, tab, q, start, sid, cnt);
+    });
 }
 
 // full scan (Alg. 3): one warp, dense r in global memory, queue pool in
@@ -175,6 +211,31 @@ __global__ void k_fill_i32(int *a, int n, int v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }
 
+template <int WPB, int HC, int NBK>
+static int launch_parallel_bit(const ScanArgs &A, int warps_wanted, cudaStream_t s) {
+    const size_t smem = (size_t)WPB * sizeof(ScanSmemBit<HC, NBK>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        MC_CUDA(cudaFuncSetAttribute(k_capforest_bit<WPB, HC, NBK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr_set = true;
+    }
+    int per_sm = 0;
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest_bit<WPB, HC, NBK>, WPB * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    int blocks = per_sm * num_sms();
+    if (warps_wanted > 0) {
+        int b = (warps_wanted + WPB - 1) / WPB;
+        if (b < blocks) blocks = b;
+    }
+    int maxb = (A.g.n + 32 * WPB - 1) / (32 * WPB);
+    if (maxb < 1) maxb = 1;
+    if (blocks > maxb) blocks = maxb;
+    ++::mc::g_launches; k_capforest_bit<WPB, HC, NBK><<<blocks, WPB * 32, smem, s>>>(A);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 template <int WPB, int HC, int NB>
 static int launch_parallel(const ScanArgs &A, int fifo, int warps_wanted, cudaStream_t s) {
     const size_t smem = (size_t)WPB * sizeof(ScanSmem<HC, NB>);
@@ -234,7 +295,19 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
     int budget = cfg.budget > 0 ? cfg.budget : 192;
     constexpr int WPB = 4;
     int rc;
-    if (budget <= 192) {
+    if (cfg.lam_hint > 0 && cfg.lam_hint < 64 && !cfg.pq_fifo && budget <= 768) {
+        // small cap: bitmap queue
+        if (budget <= 192) {
+            A.limit = budget;
+            rc = launch_parallel_bit<WPB, 256, 64>(A, cfg.warps, s);
+        } else if (budget <= 384 - 32) {
+            A.limit = budget;
+            rc = launch_parallel_bit<WPB, 512, 64>(A, cfg.warps, s);
+        } else {
+            A.limit = budget;
+            rc = launch_parallel_bit<WPB, 1024, 64>(A, cfg.warps, s);
+        }
+    } else if (budget <= 192) {
         A.limit = budget;
         rc = launch_parallel<WPB, 256, 256>(A, cfg.pq_fifo, cfg.warps, s);
     } else if (budget <= 384 - 32) {

@@ -161,9 +161,9 @@ template <> struct LogHC<512> { static constexpr int v = 9; };
 template <> struct LogHC<1024> { static constexpr int v = 10; };
 template <> struct LogHC<2048> { static constexpr int v = 11; };
 
-template <int HC, int NB>
+template <int HC, class SM>
 struct HashTable {
-    ScanSmem<HC, NB> *sm;
+    SM *sm;
     int limit;
     __device__ __forceinline__ int *val() const { return sm->val; }
     // slot of y, inserting it; -1 if the table refuses a new vertex
@@ -239,10 +239,18 @@ __device__ void pq_rebuild(BucketQ<unsigned short, NB> &q, ScanSmem<HC, NB> &sm)
 
 // One scan of Alg. 1 from `start` with id `sid` and key cap C.
 template <int HC, int NB>
-template <class Q>
-__device__ bool HashTable<HC, NB>::rebuild(Q &q) const {
-    pq_rebuild(q, *sm);
+__device__ __forceinline__ bool hash_rebuild(BucketQ<unsigned short, NB> &q, ScanSmem<HC, NB> &sm) {
+    pq_rebuild(q, sm);
     return true;
+}
+template <class Q, class SM>
+__device__ __forceinline__ bool hash_rebuild(Q &, SM &) {
+    return true;  // the bitmap queue never runs out of room
+}
+template <int HC, class SM>
+template <class Q>
+__device__ bool HashTable<HC, SM>::rebuild(Q &q) const {
+    return hash_rebuild(q, *sm);
 }
 
 template <class Q>
@@ -262,7 +270,89 @@ __device__ bool DenseTable::rebuild(Q &q) const {
     return true;
 }
 
-template <class Table, class Q>
+// ---------------------------------------------------- generic queue ops --
+// q_update: lanes with `want` move `slot` from key ko (-1: not queued) to kn.
+// q_pop: a slot of maximum key, removed, or -1 when empty.
+template <class Idx, int NB>
+__device__ __forceinline__ bool q_changed(const BucketQ<Idx, NB> &q, int ko, int kn) {
+    return q.bucket(kn) != q.bucket(ko);
+}
+template <class Idx, int NB>
+__device__ __forceinline__ bool q_update(BucketQ<Idx, NB> &q, bool want, int s, int ko, int kn) {
+    (void)ko;
+    return pq_push(q, want, s, kn);
+}
+template <class Idx, int NB>
+__device__ __forceinline__ int q_pop(BucketQ<Idx, NB> &q, const int *rv) {
+    return pq_pop(q, rv);
+}
+
+// Bitmap bucket queue for small caps (C < NBK <= 64) over a table of HC <=
+// 1024 slots: bucket b is a bitmap of its slots plus a member count.  A key
+// change clears the slot's bit in the old bucket and sets it in the new one,
+// so the queue never holds stale entries; a pop takes the lowest slot of the
+// highest non-empty bucket (a fixed tie rule, like LIFO/FIFO any order among
+// equal keys is valid).
+template <int HC, int NBK>
+struct BitQ {
+    static constexpr int W = HC / 32;
+    u32 *bits;  // NBK x W words
+    int *cnt;   // NBK counts
+    int C;
+    bool coarse = false;
+    __device__ __forceinline__ int bucket(int k) const { return k; }
+};
+template <int HC, int NBK>
+__device__ __forceinline__ bool q_changed(const BitQ<HC, NBK> &q, int ko, int kn) {
+    return ko != kn;
+}
+template <int HC, int NBK>
+__device__ __forceinline__ bool q_update(BitQ<HC, NBK> &q, bool want, int s, int ko, int kn) {
+    if (want) {
+        const u32 bit = 1u << (s & 31);
+        const int wd = s >> 5;
+        if (ko >= 0) {
+            atomicAnd(&q.bits[ko * BitQ<HC, NBK>::W + wd], ~bit);
+            atomicSub(&q.cnt[ko], 1);
+        }
+        atomicOr(&q.bits[kn * BitQ<HC, NBK>::W + wd], bit);
+        atomicAdd(&q.cnt[kn], 1);
+    }
+    __syncwarp();
+    return true;
+}
+template <int HC, int NBK>
+__device__ __forceinline__ int q_pop(BitQ<HC, NBK> &q, const int *) {
+    static_assert(HC / 32 <= 32 && NBK <= 64, "bitmap queue bounds");
+    const int lane = threadIdx.x & 31;
+    int top = -1;
+#pragma unroll
+    for (int b0 = ((NBK - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
+        const int b = b0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, b < NBK && b <= q.C && q.cnt[b] > 0);
+        if (top < 0 && m) top = b0 + 31 - __clz(m);
+    }
+    if (top < 0) return -1;
+    constexpr int W = BitQ<HC, NBK>::W;
+    const u32 word = lane < W ? q.bits[top * W + lane] : 0u;
+    const unsigned m = __ballot_sync(0xffffffffu, word != 0u);
+    const int wl = __ffs(m) - 1;
+    const u32 wv = __shfl_sync(0xffffffffu, word, wl);
+    const int s = wl * 32 + __ffs(wv) - 1;
+    __syncwarp();
+    if (lane == 0) {
+        q.bits[top * W + wl] = wv & (wv - 1u);
+        q.cnt[top] -= 1;
+    }
+    __syncwarp();
+    return s;
+}
+
+// A scan with PRECHECK looks up the owner of every vertex it touches for the
+// first time: a vertex another scan already owns is blacklisted right away
+// (Alg. 1's blacklisting, taken before any of its arcs count, so it never
+// enters this scan's r-values -- Lemma 2 part 3).
+template <class Table, class Q, bool PRECHECK = false>
 __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt) {
     const int lane = threadIdx.x & 31;
     const int n = A.g.n;
@@ -271,14 +361,14 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
     {
         int s = lane == 0 ? tab.find(start) : 0;
         s = __shfl_sync(0xffffffffu, s, 0);
-        pq_push(q, lane == 0, s, 0);
+        q_update(q, lane == 0, s, -1, 0);
     }
     long long alpha = 0, best = LLONG_MAX;
     int nS = 0, best_len = 0;
     bool alpha_ok = true, stop = false;
     cnt.scans++;
     while (!stop) {
-        int s = pq_pop(q, rv);
+        int s = q_pop(q, rv);
         if (s < 0) break;
         int x = tab.vertex(s);
         int rx = rv[s];
@@ -331,9 +421,14 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             // the cut of S, but the scan goes on over the vertices it holds
             if (__any_sync(0xffffffffu, v && s2 < 0)) alpha_ok = false;
             bool push = false;
-            int kn = 0;
+            int kn = 0, ko = -1;
             if (s2 >= 0) {
                 int r_old = rv[s2];
+                if (PRECHECK && r_old == 0 && *(volatile int *)&A.T[y] != 0) {
+                    rv[s2] = kDone;  // owned by another scan: blacklisted
+                    cnt.black++;
+                    r_old = kDone;
+                }
                 if (r_old != kDone) {
                     int r_new = sat_add(r_old, c);
                     rv[s2] = r_new;
@@ -341,14 +436,15 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
                     if ((long long)r_old < L && L <= (long long)r_new && L <= (long long)C) {
                         if (uf_union(A.par, x, y)) cnt.unions++;
                     }
-                    int ko = r_old < C ? r_old : C;
+                    const int kold = r_old < C ? r_old : C;
                     kn = r_new < C ? r_new : C;
-                    push = r_old == 0 || q.bucket(kn) != q.bucket(ko);
+                    push = r_old == 0 || q_changed(q, kold, kn);
+                    ko = r_old == 0 ? -1 : kold;
                 }
             }
             // a full pool is rebuilt from the live slots (they already hold
             // this chunk's new keys); a table that cannot rebuild ends the scan
-            if (!pq_push(q, push, s2, kn) && !tab.rebuild(q)) {
+            if (!q_update(q, push, s2, ko, kn) && !tab.rebuild(q)) {
                 stop = true;
                 alpha_ok = false;
             }
@@ -360,6 +456,16 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         A.rec_len[sid] = best_len;
     }
 }
+
+// shared memory of one warp's scan with the bitmap queue
+template <int HC, int NBK>
+struct ScanSmemBit {
+    int key[HC];
+    int val[HC];
+    u32 bits[NBK * (HC / 32)];
+    int cnt[NBK];
+    int used;
+};
 
 template <int HC_, int NB_>
 struct SmemQ : BucketQ<unsigned short, NB_> {

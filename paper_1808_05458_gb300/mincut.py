@@ -425,9 +425,7 @@ def batch_autotune(row_ptr, col, w, vtx_off, arc_off, opts: McOptions | None = N
     o = opts if opts is not None else options()
     _check(lib.mc_batch_autotune(len(vo) - 1, _ptr(vo), _ptr(ao), _ptr(rp), _ptr(c), _ptr(ww),
                                  ctypes.byref(o), ctypes.byref(best), _ptr(ms), 16),
-           "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
-           "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
-           "mc_proposer_bound")
+           "mc_batch_autotune")
     return best.value, ms
 
 
