@@ -74,6 +74,11 @@ typedef struct mc_options {
     uint64_t seed;           /* start vertices / LP parity                      */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = the graph's own */
     void *proposer;          /* mc_proposer* for MC_BOUND_LEARNED / _BEST      */
+    int32_t tail_vertices;   /* once the contracted graph has at most this many
+                                vertices and 64 arcs per vertex, its remaining
+                                rounds run in one single-warp launch; 0 = the
+                                default (256), < 0 = never; at most 4096       */
+    int32_t reserved_;       /* must be 0                                       */
 } mc_options;
 
 /* Per-call statistics (all optional). */
@@ -95,6 +100,9 @@ typedef struct mc_stats {
     int32_t scan_launches;   /* launches of the concurrent-scan kernel          */
     int32_t pad_;
     double ms_scan_kernel;   /* device time of those launches (events)          */
+    double ms_tail;          /* single-warp tail solver (see tail_vertices)     */
+    int32_t tail_launches;   /* 1 if the tail solver finished the call          */
+    int32_t pad2_;
 } mc_stats;
 
 typedef struct mc_graph mc_graph; /* opaque; owns its device copies */

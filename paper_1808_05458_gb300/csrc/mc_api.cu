@@ -171,10 +171,10 @@ int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool ve
                     (long long)cur.arcs, nc);
         if (nc < 2 || (long long)nc * 10 > (long long)cur.n * 9) break;
         MC_TRY(round_reset(w, lam, s));
-        MC_TRY(contract_graph(cur, *nxt, w, lam, false, nc, s));
-        MC_TRY(orig_update(w, n0, s));
-        MC_TRY(min_degree(*nxt, w, s));
-        MC_TRY(status_read(w, s));
+        MC_TRY(contract_graph(cur, *nxt, w, lam, false, nc, s, [&]() -> int {
+            MC_TRY(orig_update(w, n0, s));
+            return min_degree(*nxt, w, s);
+        }));
         bytes += cur.arcs * 20;
         if (w.h_st->mindeg < lam) {
             lam = w.h_st->mindeg;
@@ -188,10 +188,10 @@ int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool ve
         MC_TRY(pr_tests_budget(cur, w, lam, 1, 4, 64, s));
         MC_TRY(status_read(w, s));
         if (w.h_st->unions > 0 && cur.n >= 2) {
-            MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s));
-            MC_TRY(orig_update(w, n0, s));
-            MC_TRY(min_degree(*nxt, w, s));
-            MC_TRY(status_read(w, s));
+            MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s, [&]() -> int {
+                MC_TRY(orig_update(w, n0, s));
+                return min_degree(*nxt, w, s);
+            }));
             if (nxt->n >= 2 && w.h_st->mindeg < lam) {
                 lam = w.h_st->mindeg;
                 MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
@@ -254,6 +254,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
     int rounds = 0, fallbacks = 0;
+    const int tail_n = o.tail_vertices == 0 ? 256 : (o.tail_vertices > 4096 ? 4096 : o.tail_vertices);
     const bool verbose = getenv("MC_VERBOSE") != nullptr;
 
     // Alg. 2's loop from `cur`, contracting into the free buffer of Ga / Gb;
@@ -262,6 +263,20 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     int guard = 0;
     while (cur.n >= 2 && lam > 0) {
         if (++guard > 4 * n0 + 64) return MC_EINTERNAL;
+        // a small remainder: its rounds in one single-warp launch
+        if (tail_n > 0 && cur.n <= tail_n && cur.arcs <= 64LL * tail_n) {
+            long long lt = lam;
+            MC_TRY(tail_solve(cur, w, tail_n, &lt, o.seed ^ (u64)rounds, o.pr_level,
+                              o.pq_order == MC_PQ_FIFO, n0, s));
+            const double t = ph.ms();
+            if (verbose)
+                fprintf(stderr, "[mc] tail n=%d arcs=%lld lam %lld -> %lld (%.3f ms)\n", cur.n,
+                        (long long)cur.arcs, (long long)lam, lt, t);
+            lam = lt;
+            S.ms_tail += t;
+            ++S.tail_launches;
+            break;
+        }
         cfg.round = rounds + guard;
         MC_TRY(union_find_init(w.par, cur.n, s));
         MC_TRY(round_reset(w, lam, s));
@@ -342,12 +357,14 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             }
         }
         S.ms_capforest += ph.ms();
-        MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s));
-        MC_TRY(orig_update(w, n0, s));
-        MC_TRY(min_degree(*nxt, w, s));
-        MC_TRY(status_read(w, s));
+        // contraction; the orig map and the new minimum degree ride on its
+        // final status read
+        MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s, [&]() -> int {
+            MC_TRY(orig_update(w, n0, s));
+            return min_degree(*nxt, w, s);
+        }));
         if (w.h_st->err & kErrOverflow) return MC_EOVERFLOW;
-        bytes += cur.arcs * 20 + w.h_st->count * 12 + (i64)cur.n * 16 + (i64)n0 * 8;
+        bytes += cur.arcs * 20 + w.last_emitted * 12 + (i64)cur.n * 16 + (i64)n0 * 8;
         if (nxt->n >= 2 && w.h_st->mindeg < lam) {
             lam = w.h_st->mindeg;
             MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
@@ -356,8 +373,8 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             double t = ph.ms();
             S.ms_contract += t;
             if (verbose)
-                fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld (%.3f ms) lam=%lld\n", nxt->n,
-                        (long long)nxt->arcs, t, (long long)lam);
+                fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld emitted=%lld (%.3f ms) lam=%lld\n", nxt->n,
+                        (long long)nxt->arcs, (long long)w.last_emitted, t, (long long)lam);
         }
         cur = *nxt;
         nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
@@ -442,7 +459,7 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out, uint32_t
     if (!g || !lambda_out) return MC_EINVAL;
     mc_options o;
     if (opt) o = *opt; else mc_options_default(&o);
-    if (o.pr_level < 0 || o.pr_level > 4) return MC_EINVAL;
+    if (o.pr_level < 0 || o.pr_level > 4 || o.reserved_ != 0) return MC_EINVAL;
     cudaStream_t s = pick_stream(g, opt);
     SolveOut so;
     int rc = solve_impl(g, o, s, so);

@@ -332,6 +332,92 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
     __syncwarp();
 }
 
+// Alg. 2's rounds on the graph in the A buffers of S (n vertices, `arcs`
+// arcs, degrees in S.deg): PR1/PR2 + degree-2 rule, one full capped scan,
+// in-warp contraction, lambda-hat = min(., delta), until one vertex is left.
+// `lam` enters as lambda-hat and leaves as the minimum found; every lowering
+// rewrites the side bitmap S.best over the n0 vertices of S.orig.
+template <int SN>
+__device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arcs, long long &lam, int &err,
+                             int &ovf, u64 seed, u64 tag, int pr_level, int fifo) {
+    const int lane = lane_id();
+    int n = n0;
+    int *rpA = S.rpA, *srcA = S.srcA, *rpB = S.rpB, *srcB = S.srcB;
+    int2 *adjA = S.adjA, *adjB = S.adjB;
+    int round = 0, guard = 0;
+    while (!err && n >= 2 && lam > 0) {
+        if (++guard > 4 * n0 + 16) { err = MC_EINTERNAL; break; }
+        for (int v = lane; v < n; v += 32) S.par[v] = v;
+        __syncwarp();
+        long long un = 0;
+        // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
+        if (pr_level >= 1) {
+            for (long long i = lane; i < arcs; i += 32) {
+                const int u = srcA[i];
+                const int2 e = adjA[i];
+                if (u >= e.x) continue;
+                const long long c = e.y, du = S.deg[u], dv = S.deg[e.x];
+                const bool ok = c >= lam || (pr_level >= 2 && 2 * c > (du < dv ? du : dv));
+                if (ok && uf_union(S.par, u, e.x)) ++un;
+            }
+            if (pr_level >= 2) {
+                for (int u = lane; u < n; u += 32) {
+                    const int a = rpA[u];
+                    if (rpA[u + 1] - a != 2) continue;
+                    const int2 e0 = adjA[a], e1 = adjA[a + 1];
+                    if (e0.y == e1.y && uf_union(S.par, u, e0.x < e1.x ? e0.x : e1.x)) ++un;
+                }
+            }
+            __syncwarp();
+        }
+        // one full capped CAPFOREST scan
+        ScanArgs A;
+        A.g.n = n; A.g.arcs = arcs; A.g.rp = rpA; A.g.src = srcA; A.g.adj = adjA; A.g.deg = S.deg;
+        A.par = S.par; A.T = S.T; A.order = S.order; A.st = S.st;
+        A.rec_alpha = S.rec_alpha; A.rec_len = S.rec_len; A.perm_a = 1; A.perm_b = 0; A.limit = 0;
+        const u64 h = splitmix64(seed ^ splitmix64((tag << 20) ^ (u64)round));
+        const int start = (int)(h % (u64)n);
+        Counters cnt;
+        warp_full_scan<SN>(A, sm, S, n, arcs, lam, start, fifo, cnt);
+        un += cnt.unions;
+        un = warp_sum_ll(un);
+        const long long lam2 = ld_volatile_i64(&S.st->lam);
+        if (lam2 < lam) {
+            const int len = S.rec_len[1];
+            warp_side_bits(S.best, n0, [&](int v) {
+                const int c = S.orig[v];
+                return S.T[c] == 1 && S.order[c] < len;
+            });
+            lam = lam2;
+            if (un == 0) { ++round; continue; }
+        }
+        if (un == 0) { err = MC_EINTERNAL; break; }
+        // contraction
+        const int nc = warp_relabel(S.par, S.root, S.lab, S.cnt, n);
+        // the result goes to the B buffers, then A and B swap roles
+        arcs = warp_contract(srcA, adjA, arcs, S.lab, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB, S.deg, S.cnt,
+                             S.mark, &ovf);
+        for (int v = lane; v < n0; v += 32) S.orig[v] = S.lab[S.orig[v]];
+        __syncwarp();
+        {
+            int *t = rpA; rpA = rpB; rpB = t;
+            t = srcA; srcA = srcB; srcB = t;
+            int2 *ta = adjA; adjA = adjB; adjB = ta;
+        }
+        n = nc;
+        if (n >= 2) {
+            long long md;
+            int arg;
+            warp_min_deg(S.deg, n, &md, &arg);
+            if (md < lam) {
+                lam = md;
+                warp_side_bits(S.best, n0, [&](int v) { return S.orig[v] == arg; });
+            }
+        }
+        ++round;
+    }
+}
+
 template <int SN>
 __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm) {
     const int lane = lane_id();
@@ -397,82 +483,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
             warp_side_bits(S.best, n0, [&](int v) { return v == arg; });
             for (int v = lane; v < n0; v += 32) S.orig[v] = v;
             __syncwarp();
-            int n = n0;
-            int *rpA = S.rpA, *srcA = S.srcA, *rpB = S.rpB, *srcB = S.srcB;
-            int2 *adjA = S.adjA, *adjB = S.adjB;
-            int round = 0, guard = 0;
-            while (!err && n >= 2 && lam > 0) {
-                if (++guard > 4 * n0 + 16) { err = MC_EINTERNAL; break; }
-                for (int v = lane; v < n; v += 32) S.par[v] = v;
-                __syncwarp();
-                long long un = 0;
-                // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
-                if (B.pr_level >= 1) {
-                    for (long long i = lane; i < arcs; i += 32) {
-                        const int u = srcA[i];
-                        const int2 e = adjA[i];
-                        if (u >= e.x) continue;
-                        const long long c = e.y, du = S.deg[u], dv = S.deg[e.x];
-                        const bool ok = c >= lam || (B.pr_level >= 2 && 2 * c > (du < dv ? du : dv));
-                        if (ok && uf_union(S.par, u, e.x)) ++un;
-                    }
-                    if (B.pr_level >= 2) {
-                        for (int u = lane; u < n; u += 32) {
-                            const int a = rpA[u];
-                            if (rpA[u + 1] - a != 2) continue;
-                            const int2 e0 = adjA[a], e1 = adjA[a + 1];
-                            if (e0.y == e1.y && uf_union(S.par, u, e0.x < e1.x ? e0.x : e1.x)) ++un;
-                        }
-                    }
-                    __syncwarp();
-                }
-                // one full capped CAPFOREST scan
-                ScanArgs A;
-                A.g.n = n; A.g.arcs = arcs; A.g.rp = rpA; A.g.src = srcA; A.g.adj = adjA; A.g.deg = S.deg;
-                A.par = S.par; A.T = S.T; A.order = S.order; A.st = S.st;
-                A.rec_alpha = S.rec_alpha; A.rec_len = S.rec_len; A.perm_a = 1; A.perm_b = 0; A.limit = 0;
-                const u64 h = splitmix64(B.seed ^ splitmix64(((u64)gi << 20) ^ (u64)round));
-                const int start = (int)(h % (u64)n);
-                Counters cnt;
-                warp_full_scan<SN>(A, sm, S, n, arcs, lam, start, B.fifo, cnt);
-                un += cnt.unions;
-                un = warp_sum_ll(un);
-                const long long lam2 = ld_volatile_i64(&S.st->lam);
-                if (lam2 < lam) {
-                    const int len = S.rec_len[1];
-                    warp_side_bits(S.best, n0, [&](int v) {
-                        const int c = S.orig[v];
-                        return S.T[c] == 1 && S.order[c] < len;
-                    });
-                    const long long before = lam;
-                    lam = lam2;
-                    if (un == 0) { ++round; (void)before; continue; }
-                }
-                if (un == 0) { err = MC_EINTERNAL; break; }
-                // contraction
-                const int nc = warp_relabel(S.par, S.root, S.lab, S.cnt, n);
-                // the result goes to the B buffers, then A and B swap roles
-                arcs = warp_contract(srcA, adjA, arcs, S.lab, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB,
-                                     S.deg, S.cnt, S.mark, &ovf);
-                for (int v = lane; v < n0; v += 32) S.orig[v] = S.lab[S.orig[v]];
-                __syncwarp();
-                {
-                    int *t = rpA; rpA = rpB; rpB = t;
-                    t = srcA; srcA = srcB; srcB = t;
-                    int2 *ta = adjA; adjA = adjB; adjB = ta;
-                }
-                n = nc;
-                if (n >= 2) {
-                    long long md;
-                    int arg;
-                    warp_min_deg(S.deg, n, &md, &arg);
-                    if (md < lam) {
-                        lam = md;
-                        warp_side_bits(S.best, n0, [&](int v) { return S.orig[v] == arg; });
-                    }
-                }
-                ++round;
-            }
+            exact_rounds<SN>(S, sm, n0, arcs, lam, err, ovf, B.seed, (u64)gi, B.pr_level, B.fifo);
         }
     }
     if (lane == 0) {
@@ -504,6 +515,39 @@ __global__ void __launch_bounds__(WPB * 32) k_batch(BatchIn B) {
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= B.G) break;
         solve_one<SN>(B, B.order[k], S0, smem[wid]);
+    }
+}
+
+// ------------------------------------------------------------ tail solver --
+constexpr int kTailSN = 2048;
+
+struct TailIn {
+    DevGraph g;
+    long long lam;
+    unsigned char *scratch;
+    Layout L;
+    u64 seed;
+    int pr_level, fifo;
+    Status *out;  // out->lam = the minimum found, out->err
+};
+
+// one warp: copy the small graph into its scratch, then Alg. 2's rounds
+__global__ void __launch_bounds__(32) k_tail(TailIn T) {
+    __shared__ WarpSmem<kTailSN> sm;
+    Scratch S = scratch_of(T.scratch, T.L);
+    const int lane = lane_id();
+    const int n = T.g.n;
+    const long long arcs = T.g.arcs;
+    for (int v = lane; v <= n; v += 32) S.rpA[v] = T.g.rp[v];
+    for (int v = lane; v < n; v += 32) { S.deg[v] = T.g.deg[v]; S.orig[v] = v; }
+    for (long long i = lane; i < arcs; i += 32) { S.srcA[i] = T.g.src[i]; S.adjA[i] = T.g.adj[i]; }
+    __syncwarp();
+    long long lam = T.lam;
+    int err = 0, ovf = 0;
+    exact_rounds<kTailSN>(S, sm, n, arcs, lam, err, ovf, T.seed, 0x7A11ULL, T.pr_level, T.fifo);
+    if (lane == 0) {
+        T.out->lam = lam;
+        T.out->err = err;
     }
 }
 
@@ -675,6 +719,41 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
     if (ms_out) *ms_out = ms;
     for (int k = 0; k < G; ++k)
         if (errs[k]) return errs[k];
+    return MC_OK;
+}
+
+int tail_solve(const DevGraph &g, Work &w, int limit, long long *lam, u64 seed, int pr_level, int fifo,
+               int n0, cudaStream_t s) {
+    if (limit > 4096) limit = 4096;
+    if (g.n > limit || g.arcs > 64LL * limit || g.n < 2) return MC_EINVAL;
+    const Layout L = make_layout(limit, 64LL * limit);
+    if (w.tail_bytes < L.bytes) {
+        dev_free(w.tail, s);
+        w.tail = nullptr;
+        w.tail_bytes = 0;
+        MC_TRY(dev_alloc(reinterpret_cast<void **>(&w.tail), L.bytes, s));
+        w.tail_bytes = L.bytes;
+    }
+    TailIn T;
+    T.g = g;
+    T.lam = *lam;
+    T.scratch = w.tail;
+    T.L = L;
+    T.seed = seed;
+    T.pr_level = pr_level;
+    T.fifo = fifo;
+    T.out = w.st;
+    ++::mc::g_launches; k_tail<<<1, 32, 0, s>>>(T);
+    MC_CUDA(cudaGetLastError());
+    MC_TRY(status_read(w, s));
+    if (w.h_st->err) {
+        set_error_detail("tail solver failed");
+        return w.h_st->err;
+    }
+    if (w.h_st->lam < *lam) {
+        MC_TRY(side_from_bits(w, n0, reinterpret_cast<const u32 *>(w.tail + L.best), s));
+        *lam = w.h_st->lam;
+    }
     return MC_OK;
 }
 

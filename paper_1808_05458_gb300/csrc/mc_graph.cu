@@ -13,6 +13,8 @@
 // it is >= lambda-hat, so the clamp changes no cut below lambda-hat.
 #include <cstdio>
 
+#include <functional>
+
 #include "mc_internal.cuh"
 
 namespace mc {
@@ -71,7 +73,7 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
 void work_free(Work &w, cudaStream_t s) {
     void *ps[] = {w.par, w.root, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
                   w.valsA, w.valsB, w.radix_tmp, w.rec_alpha, w.rec_len, w.fb_r, w.fb_pool,
-                  w.best_side, w.st};
+                  w.best_side, w.st, w.tail};
     for (void *p : ps) dev_free(p, s);
     if (w.h_st) cudaFreeHost(w.h_st);
     w = Work();
@@ -109,71 +111,154 @@ __global__ void k_relabel(const int *__restrict__ root, int *lab, int n) {
 }
 
 // ------------------------------------------------------------- emitting ---
-// one (block(u), block(v), c) arc per arc with different blocks; warp-wide
-// compaction through a single counter
-__global__ void k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs,
-                       const int *__restrict__ lab, u64 nc, u64 *__restrict__ keys,
-                       int *__restrict__ vals, u64 *counter) {
+// Block-chunked compaction: each block takes chunks of kEmitItems x 256 arcs,
+// keeps its survivors in registers, ranks them with one block scan and
+// reserves their output range with a single atomic per chunk (a per-warp
+// atomic on one global counter serialises millions of times).
+constexpr int kEmitItems = 8;
+constexpr int kEmitChunk = kEmitItems * kThreads;
+
+__device__ __forceinline__ int block_excl_scan_256(int v, int *total) {
+    __shared__ int ws[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int x = lane < kThreads / 32 ? ws[lane] : 0;
+        int xs = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += t;
+        }
+        if (lane < kThreads / 32) ws[lane] = xs - x;
+        if (lane == kThreads / 32 - 1) *total = xs;
+    }
+    __syncthreads();
+    const int r = ws[wid] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+// one (block(u), block(v), c) arc per arc with different blocks.  Within a
+// warp's 32 consecutive arcs, a run of equal (block(u), block(v)) keys is
+// emitted once by its first lane with the run's weight added up, saturated at
+// min(clamp, INT32_MAX): the later segmented sum of saturated parts,
+// saturated again, equals the saturated total.
+__global__ void __launch_bounds__(kThreads)
+k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs, const int *__restrict__ lab,
+       u64 nc, const int *d_nc, i64 clamp, u64 *__restrict__ keys, int *__restrict__ vals, u64 *counter,
+       int *err) {
+    __shared__ int total;
+    __shared__ u64 base_s;
+    if (d_nc) nc = (u64)*d_nc;
+    const long long cap = clamp < (i64)kInt32Max ? clamp : (i64)kInt32Max;
     const int lane = threadIdx.x & 31;
-    const i64 stride = (i64)gridDim.x * blockDim.x;
-    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < arcs; i0 += stride) {
-        i64 i = i0 + lane;
-        bool ok = i < arcs;
-        int a = 0, b = 0, c = 0;
-        if (ok) {
-            int2 e = adj[i];
-            a = lab[src[i]];
-            b = lab[e.x];
-            c = e.y;
-            ok = a != b;
+    for (i64 c0 = (i64)blockIdx.x * kEmitChunk; c0 < arcs; c0 += (i64)gridDim.x * kEmitChunk) {
+        u64 key[kEmitItems];
+        int val[kEmitItems];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kEmitItems; ++k) {
+            const i64 i = c0 + (i64)k * kThreads + threadIdx.x;
+            u64 kk = ~0ULL;
+            long long c = 0;
+            if (i < arcs) {
+                const int2 e = adj[i];
+                const int a = lab[src[i]], b = lab[e.x];
+                if (a != b) {
+                    kk = (u64)a * nc + (u64)b;
+                    c = e.y;
+                }
+            }
+            // runs of equal keys among the warp's lanes: sum toward the first
+            const u64 kp = __shfl_up_sync(0xffffffffu, kk, 1);
+            const bool head = lane == 0 || kp != kk;
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const int run = __popc(hm & ((2u << lane) - 1u));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_down_sync(0xffffffffu, c, o);
+                const int ro = __shfl_down_sync(0xffffffffu, run, o);
+                if (lane + o < 32 && ro == run) c += t;
+            }
+            key[k] = ~0ULL;
+            if (head && kk != ~0ULL) {
+                if (c > (long long)kInt32Max && clamp > (i64)kInt32Max) atomicOr(err, kErrOverflow);
+                key[k] = kk;
+                val[k] = (int)(c > cap ? cap : c);
+                ++cnt;
+            }
         }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (!m) continue;
-        u64 base = 0;
-        if (lane == 0) base = atomicAdd(counter, (u64)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok) {
-            u64 pos = base + __popc(m & ((1u << lane) - 1u));
-            keys[pos] = (u64)a * nc + (u64)b;
-            vals[pos] = c;
-        }
+        const int off = block_excl_scan_256(cnt, &total);
+        if (threadIdx.x == 0) base_s = total ? atomicAdd(counter, (u64)total) : 0;
+        __syncthreads();
+        u64 pos = base_s + off;
+#pragma unroll
+        for (int k = 0; k < kEmitItems; ++k)
+            if (key[k] != ~0ULL) { keys[pos] = key[k]; vals[pos] = val[k]; ++pos; }
+        __syncthreads();
     }
 }
 
 // raw input arcs: validate and emit (u, v, c) for u != v, c > 0
-__global__ void k_emit_raw(const int *__restrict__ rp, const int *__restrict__ col,
-                           const int *__restrict__ w, int n, i64 arcs, u64 *__restrict__ keys,
-                           int *__restrict__ vals, u64 *counter, int *err) {
-    const int lane = threadIdx.x & 31;
-    const i64 stride = (i64)gridDim.x * blockDim.x;
-    for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < arcs; i0 += stride) {
-        i64 i = i0 + lane;
-        bool ok = i < arcs;
-        int u = 0, v = 0, c = 0;
-        if (ok) {
-            // source row by binary search: largest u with rp[u] <= i
+__global__ void __launch_bounds__(kThreads)
+k_emit_raw(const int *__restrict__ rp, const int *__restrict__ col, const int *__restrict__ w, int n,
+           i64 arcs, u64 *__restrict__ keys, int *__restrict__ vals, u64 *counter, int *err) {
+    __shared__ int total;
+    __shared__ u64 base_s;
+    for (i64 c0 = (i64)blockIdx.x * kEmitChunk; c0 < arcs; c0 += (i64)gridDim.x * kEmitChunk) {
+        u64 key[kEmitItems];
+        int val[kEmitItems];
+        int cnt = 0;
+        // source row: largest u with rp[u] <= i, by binary search
+        int u = 0;
+        {
             int lo = 0, hi = n - 1;
+            const i64 first = c0 + threadIdx.x;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if ((i64)rp[mid] <= i) lo = mid; else hi = mid - 1;
+                const int mid = (lo + hi + 1) >> 1;
+                if ((i64)rp[mid] <= first) lo = mid; else hi = mid - 1;
             }
             u = lo;
-            v = col[i];
-            c = w[i];
-            if (v < 0 || v >= n) { atomicOr(err, kErrRange); ok = false; }
-            else if (c < 0) { atomicOr(err, kErrNegW); ok = false; }
-            else ok = (u != v) && (c > 0);
         }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (!m) continue;
-        u64 base = 0;
-        if (lane == 0) base = atomicAdd(counter, (u64)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok) {
-            u64 pos = base + __popc(m & ((1u << lane) - 1u));
-            keys[pos] = (u64)u * (u64)n + (u64)v;
-            vals[pos] = c;
+#pragma unroll
+        for (int k = 0; k < kEmitItems; ++k) {
+            const i64 i = c0 + (i64)k * kThreads + threadIdx.x;
+            key[k] = ~0ULL;
+            if (i < arcs) {
+                if (u + 1 < n && (i64)rp[u + 1] <= i) {  // rows are non-decreasing: search past u
+                    int lo = u + 1, hi = n - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((i64)rp[mid] <= i) lo = mid; else hi = mid - 1;
+                    }
+                    u = lo;
+                }
+                const int v = col[i], c = w[i];
+                if (v < 0 || v >= n) atomicOr(err, kErrRange);
+                else if (c < 0) atomicOr(err, kErrNegW);
+                else if (u != v && c > 0) {
+                    key[k] = (u64)u * (u64)n + (u64)v;
+                    val[k] = c;
+                    ++cnt;
+                }
+            }
         }
+        const int off = block_excl_scan_256(cnt, &total);
+        if (threadIdx.x == 0) base_s = total ? atomicAdd(counter, (u64)total) : 0;
+        __syncthreads();
+        u64 pos = base_s + off;
+#pragma unroll
+        for (int k = 0; k < kEmitItems; ++k)
+            if (key[k] != ~0ULL) { keys[pos] = key[k]; vals[pos] = val[k]; ++pos; }
+        __syncthreads();
     }
 }
 
@@ -222,9 +307,10 @@ __global__ void k_seg_sum(const u64 *__restrict__ keys, const int *__restrict__ 
 }
 
 // clamp the summed weights, store them, and accumulate degrees
-__global__ void k_finalize(const u64 *__restrict__ acc, i64 m, i64 clamp, const int *__restrict__ osrc,
+__global__ void k_finalize(const u64 *__restrict__ acc, const int *d_m, i64 clamp, const int *__restrict__ osrc,
                            int2 *__restrict__ oadj, unsigned long long *deg, int *err) {
     const int lane = threadIdx.x & 31;
+    const i64 m = *d_m;
     const i64 stride = (i64)gridDim.x * blockDim.x;
     for (i64 i0 = (i64)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < m; i0 += stride) {
         i64 i = i0 + lane;
@@ -246,7 +332,8 @@ __global__ void k_finalize(const u64 *__restrict__ acc, i64 m, i64 clamp, const 
 }
 
 // CSR offsets from the sorted sources
-__global__ void k_rowptr(const int *__restrict__ osrc, i64 m, int nc, int *__restrict__ rp) {
+__global__ void k_rowptr(const int *__restrict__ osrc, const int *d_m, int nc, int *__restrict__ rp) {
+    const i64 m = d_m ? *d_m : 0;
     for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j <= m; j += (i64)gridDim.x * blockDim.x) {
         int prev = j == 0 ? -1 : osrc[j - 1];
         int cur = j == m ? nc : osrc[j];
@@ -301,8 +388,11 @@ static int bits_for(u64 x) {
     return b;
 }
 
-// sorted (keys, vals) of m arcs over nc vertices -> out graph (+ degrees)
-static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cudaStream_t s) {
+// sorted (keys, vals) of m arcs over nc vertices -> out graph (+ degrees).
+// The merged arc count stays on the device until the one status read at the
+// end; `post` (may be empty) launches more work before that read.
+static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cudaStream_t s,
+                            const std::function<int()> &post) {
     bool in_b = false;
     MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, m, bits_for((u64)nc * (u64)nc - 1),
                             w.radix_tmp, w.scan_tmp, &in_b, s));
@@ -311,48 +401,48 @@ static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cu
     int *flags = in_b ? w.valsA : w.valsB;      // free int32 buffer
     u64 *acc = in_b ? w.keysA : w.keysB;        // free 64-bit buffer
     int *d_total = reinterpret_cast<int *>(&w.st->count2);
-    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    MC_CUDA(cudaMemsetAsync(&w.st->count2, 0, sizeof(w.st->count2), s));
+    MC_CUDA(cudaMemsetAsync(out.deg, 0, sizeof(i64) * (size_t)nc, s));
     if (m > 0) {
         ++::mc::g_launches; k_heads<<<grid_for(m), kThreads, 0, s>>>(keys, m, flags);
         MC_TRY(exclusive_scan_i32(flags, flags, m, d_total, w.scan_tmp, s));
-    }
-    MC_TRY(status_read(w, s));
-    const i64 mu = m > 0 ? (i64)(int)w.h_st->count2 : 0;
-    out.n = nc;
-    out.arcs = mu;
-    MC_CUDA(cudaMemsetAsync(out.deg, 0, sizeof(i64) * (size_t)nc, s));
-    if (mu > 0) {
-        MC_CUDA(cudaMemsetAsync(acc, 0, sizeof(u64) * (size_t)mu, s));
+        MC_CUDA(cudaMemsetAsync(acc, 0, sizeof(u64) * (size_t)m, s));
         ++::mc::g_launches; k_seg_sum<<<grid_for(m), kThreads, 0, s>>>(keys, vals, flags, m, (u64)nc, acc, out.src,
                                                    out.adj);
-        ++::mc::g_launches; k_finalize<<<grid_for(mu), kThreads, 0, s>>>(acc, mu, clamp, out.src, out.adj,
-                                                     reinterpret_cast<unsigned long long *>(out.deg),
-                                                     &w.st->err);
+        ++::mc::g_launches; k_finalize<<<grid_for(m), kThreads, 0, s>>>(acc, d_total, clamp, out.src, out.adj,
+                                                    reinterpret_cast<unsigned long long *>(out.deg),
+                                                    &w.st->err);
     }
-    ++::mc::g_launches; k_rowptr<<<grid_for(mu + 1), kThreads, 0, s>>>(out.src, mu, nc, out.rp);
+    ++::mc::g_launches; k_rowptr<<<grid_for(m + 1), kThreads, 0, s>>>(out.src, m > 0 ? d_total : nullptr, nc, out.rp);
     MC_CUDA(cudaGetLastError());
+    out.n = nc;
+    if (post) MC_TRY(post());
+    MC_TRY(status_read(w, s));
+    out.arcs = m > 0 ? (i64)(int)w.h_st->count2 : 0;
     return MC_OK;
 }
 
 int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool flatten, int nc,
-                   cudaStream_t s) {
+                   cudaStream_t s, const std::function<int()> &post) {
     const int n = in.n;
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    const int *d_nc = nullptr;
     if (flatten) {
         ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n);
-        int *d_total = reinterpret_cast<int *>(&w.st->count);
-        ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
-        MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, d_total, w.scan_tmp, s));
+        d_nc = reinterpret_cast<int *>(&w.st->count);
+        MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
         ++::mc::g_launches; k_relabel<<<grid_for(n), kThreads, 0, s>>>(w.root, w.lab, n);
-        MC_TRY(status_read(w, s));
-        nc = (int)w.h_st->count;
     }
-    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
-    ++::mc::g_launches; k_emit<<<grid_for(in.arcs), kThreads, 0, s>>>(in.src, in.adj, in.arcs, w.lab, (u64)nc, w.keysA,
-                                                  w.valsA, reinterpret_cast<u64 *>(&w.st->count));
+    // block count (device) and emitted arcs in one status read
+    ++::mc::g_launches; k_emit<<<grid_for((in.arcs + kEmitItems - 1) / kEmitItems), kThreads, 0, s>>>(
+        in.src, in.adj, in.arcs, w.lab, (u64)nc, d_nc, clamp, w.keysA, w.valsA,
+        reinterpret_cast<u64 *>(&w.st->count2), &w.st->err);
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(w, s));
-    const i64 m = w.h_st->count;
-    return build_from_pairs(m, nc, clamp, out, w, s);
+    if (flatten) nc = (int)w.h_st->count;
+    const i64 m = w.h_st->count2;
+    w.last_emitted = m;
+    return build_from_pairs(m, nc, clamp, out, w, s, post);
 }
 
 // binary search in the sorted row of v for u; mirror weight or -1
@@ -388,14 +478,14 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     MC_CUDA(cudaStreamSynchronize(s));
     if (arcs_raw < 0 || (i64)arcs_raw > wk.cap_arcs) return MC_EINVAL;
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
-    ++::mc::g_launches; k_emit_raw<<<grid_for(arcs_raw), kThreads, 0, s>>>(rp, col, w, n, arcs_raw, wk.keysA, wk.valsA,
+    ++::mc::g_launches; k_emit_raw<<<grid_for(((i64)arcs_raw + kEmitItems - 1) / kEmitItems), kThreads, 0, s>>>(rp, col, w, n, arcs_raw, wk.keysA, wk.valsA,
                                                        reinterpret_cast<u64 *>(&wk.st->count),
                                                        &wk.st->err);
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err) return MC_EINVAL;
     const i64 m = wk.h_st->count;
-    MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s));
+    MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s, {}));
     if (check_sym && out.arcs > 0) {
         ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err);
         MC_CUDA(cudaGetLastError());
@@ -566,6 +656,21 @@ int compact_labels(Work &w, int n, int *nc, cudaStream_t s) {
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(w, s));
     *nc = (int)w.h_st->count;
+    return MC_OK;
+}
+
+struct SideBits {
+    const int *orig;
+    const u32 *bits;
+    __device__ bool operator()(int v) const {
+        const int c = orig[v];
+        return (bits[c >> 5] >> (c & 31)) & 1u;
+    }
+};
+
+int side_from_bits(Work &w, int n0, const u32 *bits, cudaStream_t s) {
+    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideBits{w.orig, bits});
+    MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
 

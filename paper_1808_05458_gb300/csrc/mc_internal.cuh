@@ -14,6 +14,7 @@
 
 #include <climits>
 
+#include <functional>
 #include <string>
 
 #include "mc.h"
@@ -139,6 +140,10 @@ struct Work {
     Status *st = nullptr;
     Status *h_st = nullptr;  // pinned mirror
     i64 cap_n = 0, cap_arcs = 0;
+    i64 last_emitted = 0;    // arcs emitted by the last contraction
+    // single-warp tail solver scratch (allocated on first use)
+    unsigned char *tail = nullptr;
+    size_t tail_bytes = 0;
 };
 
 int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s);
@@ -155,8 +160,10 @@ int status_read(Work &w, cudaStream_t s);
 // (st->mindeg / st->argmin) and w.lab (old vertex -> new vertex).  Merged
 // weights are clamped to `clamp` (> 0).  If `flatten` is false, w.lab holds
 // ready labels in [0, nc) with nc given.
+// `post` (may be empty) launches more work before the final status read,
+// whose Status copy the caller may then use; w.last_emitted = arcs emitted.
 int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool flatten, int nc,
-                   cudaStream_t s);
+                   cudaStream_t s, const std::function<int()> &post = {});
 
 // canonicalise raw CSR arrays (device) into `out` (drops self-loops / zero
 // weights, sums parallel arcs, sorts rows); checks symmetry if asked.
@@ -214,6 +221,12 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
                 const int *col, const int *w, const mc_options &o, long long *lambdas, u32 *bitmaps,
                 const long long *bitmap_word_off, int shape, double *ms_out);
 int batch_shapes();
+// the remaining rounds of Alg. 2 on a small graph g in one single-warp launch
+// (PR1/PR2 + degree-2 rule, full capped scan, in-warp contraction per
+// round); *lam = min(*lam, lambda(g)), the side recorded through w.orig
+int tail_solve(const DevGraph &g, Work &w, int limit, long long *lam, u64 seed, int pr_level, int fifo,
+               int n0, cudaStream_t s);
+int side_from_bits(Work &w, int n0, const u32 *bits, cudaStream_t s);  // bit v = bits[orig[v]]
 void batch_set_shape(int shape);
 int batch_get_shape();
 

@@ -39,7 +39,8 @@ class McOptions(ctypes.Structure):
                 ("pr_level", ctypes.c_int32), ("scans_per_round", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("lp_iters", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("proposer", ctypes.c_void_p)]
+                ("proposer", ctypes.c_void_p), ("tail_vertices", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 class McStats(ctypes.Structure):
@@ -51,7 +52,8 @@ class McStats(ctypes.Structure):
                 ("bytes_alg", ctypes.c_int64), ("scanned_arcs", ctypes.c_int64),
                 ("scanned_verts", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("scan_launches", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("ms_scan_kernel", ctypes.c_double)]
+                ("ms_scan_kernel", ctypes.c_double), ("ms_tail", ctypes.c_double),
+                ("tail_launches", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -138,7 +140,8 @@ def _ptr(a):
 
 def options(**kw) -> McOptions:
     """Default options with overrides (pq_order, bound, pr_level,
-    scans_per_round, region_budget, lp_iters, seed, cuda_stream)."""
+    scans_per_round, region_budget, lp_iters, seed, cuda_stream, proposer,
+    tail_vertices)."""
     o = McOptions()
     load_library().mc_options_default(ctypes.byref(o))
     for k, v in kw.items():

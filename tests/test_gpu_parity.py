@@ -166,7 +166,9 @@ def test_random_tiny_min_cut(mc):
             continue
         ref = oracle.brute_force(*g)[0]
         with mc.Graph(*g) as G:
-            res = G.min_cut(mc.options(seed=i, pq_order=i % 2, pr_level=i % 5))
+            # a third of the cases skip the single-warp tail solver
+            res = G.min_cut(mc.options(seed=i, pq_order=i % 2, pr_level=i % 5,
+                                       tail_vertices=-1 if i % 3 == 0 else 0))
         check_cut(mc, g, res, ref)
 
 
@@ -220,6 +222,32 @@ def test_medium_random_vs_stoer_wagner(mc):
             with mc.Graph(*g) as G:
                 res = G.min_cut(mc.options(seed=seed, pq_order=seed))
             check_cut(mc, g, res, ref)
+
+
+@pytest.mark.parametrize("tail", [-1, 64, 1024, 4096])
+def test_tail_solver_sizes(mc, tail):
+    # the single-warp tail takes over at different sizes (4096: from the
+    # start, with its r-values in global memory past 2048 vertices)
+    cases = [graphgen.random_connected(300 + 400 * i, 900 + 1500 * i, seed=70 + i, wmax=[1, 9, 60][i % 3])
+             for i in range(5)] + [graphgen.two_cliques(300, 5, seed=3), graphgen.planted(0)]
+    for i, g in enumerate(cases):
+        ref = oracle.stoer_wagner(*g)[0] if len(g[0]) <= 2000 else oracle.noi(*g)[0]
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(seed=i, tail_vertices=tail))
+        check_cut(mc, g, res, ref)
+        n, arcs = len(g[0]) - 1, len(g[1])
+        if tail == 4096 and n <= 4096 and arcs <= 64 * 4096:
+            assert res.stats["tail_launches"] == 1 and res.stats["rounds"] == 0
+        if tail == -1:
+            assert res.stats["tail_launches"] == 0
+
+
+def test_tail_option_checks(mc):
+    g = graphgen.cycle(10, 3)
+    with mc.Graph(*g) as G:
+        with pytest.raises(mc.MinCutError):
+            G.min_cut(mc.options(reserved_=1))
+        assert G.min_cut(mc.options(tail_vertices=1 << 20)).lam == 6
 
 
 @pytest.mark.parametrize("seed", range(10))
