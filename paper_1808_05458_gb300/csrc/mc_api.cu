@@ -24,7 +24,6 @@ struct mc_graph {
     i64 arcs0 = 0;
     DevGraph G0, Ga, Gb;
     Work w;
-    int ncomp = 1;
     i64 delta0 = 0;
     int argmin0 = 0;
     bool device_ptrs = false;
@@ -138,7 +137,6 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
         g->argmin0 = g->w.h_st->argmin;
         if (g->delta0 >= (1LL << 62)) rc = MC_EOVERFLOW;
     }
-    if (rc == MC_OK) rc = connected_components(g->G0, g->w, &g->ncomp, s);
     if (rc != MC_OK) {
         destroy_all(g);
         return rc;
@@ -231,16 +229,26 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } ev_free{ka, kb};
 
-    if (g->ncomp > 1) {
+    // Components are found only where they matter: a disconnected graph has
+    // lambda = 0, which the exact loop reaches by itself (a scan that covers
+    // a whole component sees alpha = 0; contraction leaves degree-0
+    // vertices); its side is then set to every component but vertex 0's.
+    auto component_side = [&](bool *disconnected) -> int {
         int nc = 0;
         MC_TRY(connected_components(g->G0, w, &nc, s));
-        MC_TRY(side_from_component(w, n0, s));
+        *disconnected = nc > 1;
+        if (nc > 1) MC_TRY(side_from_component(w, n0, s));
+        return MC_OK;
+    };
+    if (g->delta0 >= (i64)0x7FFFFFFE - 1) {
+        bool disc = false;
+        MC_TRY(component_side(&disc));
+        if (!disc) return MC_EOVERFLOW;
         MC_TRY(side_canon(w, n0, s));
         out.lam = 0;
         S.ms_total = total.ms();
         return MC_OK;
     }
-    if (g->delta0 >= (i64)0x7FFFFFFE - 1) return MC_EOVERFLOW;
 
     // lambda-hat = delta with the trivial cut of a minimum-degree vertex
     MC_TRY(iota_i32(w.orig, n0, s));
@@ -408,6 +416,10 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     rounds = 0;
     MC_TRY(exact_loop(g->G0, &g->Ga));
     (void)bound_rounds;
+    if (lam == 0) {
+        bool disc = false;
+        MC_TRY(component_side(&disc));
+    }
     MC_TRY(side_canon(w, n0, s));
     S.rounds = rounds;
     S.fallback_rounds = fallbacks;

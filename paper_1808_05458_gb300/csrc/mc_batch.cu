@@ -566,7 +566,7 @@ int grow(void **p, size_t *cur, size_t want, cudaStream_t s) {
     if (*cur >= want) return MC_OK;
     if (*p) {
         cudaStreamSynchronize(s);
-        cudaFree(*p);
+        dev_free(*p, s);
         *p = nullptr;
         *cur = 0;
     }

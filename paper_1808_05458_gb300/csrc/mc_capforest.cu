@@ -299,7 +299,11 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
         // small cap: bitmap queue
         if (budget <= 192) {
             A.limit = budget;
-            rc = launch_parallel_bit<WPB, 256, 64>(A, cfg.warps, s);
+            // as few buckets as the cap needs: less shared memory per warp,
+            // more resident warps
+            if (cfg.lam_hint < 8) rc = launch_parallel_bit<WPB, 256, 8>(A, cfg.warps, s);
+            else if (cfg.lam_hint < 32) rc = launch_parallel_bit<WPB, 256, 32>(A, cfg.warps, s);
+            else rc = launch_parallel_bit<WPB, 256, 64>(A, cfg.warps, s);
         } else if (budget <= 384 - 32) {
             A.limit = budget;
             rc = launch_parallel_bit<WPB, 512, 64>(A, cfg.warps, s);

@@ -457,15 +457,64 @@ __device__ __forceinline__ int find_arc(const int *rp, const int2 *adj, int v, i
     return -1;
 }
 
-__global__ void k_check_sym(const DevGraph g, int *err) {
+// Symmetry: every arc (u, v, c) with u < v has its mirror (v, u, c), and as
+// many arcs run downwards as upwards.  Rows hold no duplicates, so the
+// mirror map from upward to downward arcs is injective, and equal counts
+// make it a bijection.
+__global__ void k_check_sym(const DevGraph g, int *err, unsigned long long *up,
+                            unsigned long long *down) {
+    long long nu = 0, nd = 0;
     for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
-        int u = g.src[j];
-        int2 e = g.adj[j];
-        if (find_arc(g.rp, g.adj, e.x, u) != e.y) atomicOr(err, kErrAsym);
+        const int u = g.src[j];
+        const int2 e = g.adj[j];
+        if (u < e.x) {
+            ++nu;
+            if (find_arc(g.rp, g.adj, e.x, u) != e.y) atomicOr(err, kErrAsym);
+        } else {
+            ++nd;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nu) atomicAdd(up, (unsigned long long)nu);
+        if (nd) atomicAdd(down, (unsigned long long)nd);
     }
 }
 
 __global__ void k_clear_err(Status *st) { st->err = 0; }
+
+// Raw CSR -> graph (sources, {neighbour, weight}, degrees) in one pass,
+// flagging whether the input was canonical already (rows strictly
+// increasing, no self-loop, weights > 0; if not, the sort path rebuilds the
+// graph) and whether it is invalid (range, negative weight).  One warp per
+// row.
+__global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict__ col,
+                              const int *__restrict__ w, int n, DevGraph out, int *err, int *noncanon) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const int a0 = rp[u], a1 = rp[u + 1];
+        long long d = 0;
+        for (int i = a0 + lane; i < a1; i += 32) {
+            const int v = col[i], c = w[i];
+            if (v < 0 || v >= n) atomicOr(err, kErrRange);
+            else if (c < 0) atomicOr(err, kErrNegW);
+            if (v == u || c <= 0 || (i > a0 && col[i - 1] >= v)) bad = true;
+            out.src[i] = u;
+            out.adj[i] = make_int2(v, c);
+            d += c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) out.deg[u] = d;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(noncanon, 1);
+}
 
 int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym, DevGraph &out,
                  Work &wk, cudaStream_t s) {
@@ -477,36 +526,103 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     MC_CUDA(cudaMemcpyAsync(&arcs_raw, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
     if (arcs_raw < 0 || (i64)arcs_raw > wk.cap_arcs) return MC_EINVAL;
+    // already canonical (the common case): built directly, no sort
+    int *noncanon = reinterpret_cast<int *>(&wk.st->count2);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
-    ++::mc::g_launches; k_emit_raw<<<grid_for(((i64)arcs_raw + kEmitItems - 1) / kEmitItems), kThreads, 0, s>>>(rp, col, w, n, arcs_raw, wk.keysA, wk.valsA,
-                                                       reinterpret_cast<u64 *>(&wk.st->count),
-                                                       &wk.st->err);
+    MC_CUDA(cudaMemcpyAsync(out.rp, rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+    ++::mc::g_launches; k_build_canon<<<grid_for((i64)n * 32), kThreads, 0, s>>>(rp, col, w, n, out, &wk.st->err,
+                                                                               noncanon);
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err) return MC_EINVAL;
-    const i64 m = wk.h_st->count;
-    MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s, {}));
+    out.n = n;
+    out.arcs = arcs_raw;
+    if (wk.h_st->count2 != 0) {
+        ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
+        ++::mc::g_launches; k_emit_raw<<<grid_for(((i64)arcs_raw + kEmitItems - 1) / kEmitItems), kThreads, 0, s>>>(
+            rp, col, w, n, arcs_raw, wk.keysA, wk.valsA, reinterpret_cast<u64 *>(&wk.st->count), &wk.st->err);
+        MC_CUDA(cudaGetLastError());
+        MC_TRY(status_read(wk, s));
+        if (wk.h_st->err) return MC_EINVAL;
+        const i64 m = wk.h_st->count;
+        MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s, {}));
+    }
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
     if (check_sym && out.arcs > 0) {
-        ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err);
+        ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(
+            out, &wk.st->err, reinterpret_cast<unsigned long long *>(&wk.st->count),
+            reinterpret_cast<unsigned long long *>(&wk.st->count2));
         MC_CUDA(cudaGetLastError());
     }
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err & kErrOverflow) return MC_EOVERFLOW;
     if (wk.h_st->err) return MC_EINVAL;
+    if (check_sym && wk.h_st->count != wk.h_st->count2) return MC_EINVAL;
     return MC_OK;
 }
 
 // ------------------------------------------------- connected components ---
-__global__ void k_cc_union(const DevGraph g, int *par) {
-    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
-        int u = g.src[j], v = g.adj[j].x;
-        if (u < v) uf_union(par, u, v);
+// Sampled union-find (the scheme of Afforest, Sutton et al. 2018): unite
+// every vertex with its first kCcSample neighbours, find the most common
+// root among a sample of vertices, then process all arcs of the vertices
+// outside that component only.  Exact on symmetric graphs: an arc between
+// the big component and a vertex w outside it is also an arc of w.
+constexpr int kCcSample = 4;
+constexpr int kCcProbe = 1024;
+
+// one thread per (vertex, sampled arc)
+__global__ void k_cc_sample(const DevGraph g, int *par) {
+    const i64 total = (i64)g.n * kCcSample;
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (i64)gridDim.x * blockDim.x) {
+        const int v = (int)(t / kCcSample), j = (int)(t % kCcSample);
+        const int i = g.rp[v] + j;
+        if (i < g.rp[v + 1]) uf_union(par, v, g.adj[i].x);
+    }
+}
+
+// most common root among kCcProbe evenly spaced vertices -> *giant
+__global__ void __launch_bounds__(kCcProbe) k_cc_giant(const int *__restrict__ root, int n, int *giant) {
+    __shared__ int key[2 * kCcProbe];
+    __shared__ int cnt[2 * kCcProbe];
+    __shared__ unsigned long long best;
+    for (int i = threadIdx.x; i < 2 * kCcProbe; i += blockDim.x) { key[i] = -1; cnt[i] = 0; }
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    const int v = (int)(((long long)threadIdx.x * n) / kCcProbe);
+    const int r = root[v];
+    unsigned h = ((unsigned)r * 2654435761u) & (2 * kCcProbe - 1);
+    while (true) {
+        const int k = atomicCAS(&key[h], -1, r);
+        if (k == -1 || k == r) break;
+        h = (h + 1) & (2 * kCcProbe - 1);
+    }
+    const int c = atomicAdd(&cnt[h], 1) + 1;
+    // largest count, then smallest root
+    atomicMax(&best, ((unsigned long long)c << 32) | (unsigned)(0x7FFFFFFF - r));
+    __syncthreads();
+    if (threadIdx.x == 0) *giant = 0x7FFFFFFF - (int)(best & 0xFFFFFFFFu);
+}
+
+__global__ void k_cc_finish(const DevGraph g, const int *__restrict__ root, const int *giant, int *par) {
+    const int G = *giant;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += nw) {
+        if (root[v] == G) continue;
+        const int a0 = g.rp[v], a1 = g.rp[v + 1];
+        for (int i = a0 + kCcSample + lane; i < a1; i += 32) uf_union(par, v, g.adj[i].x);
     }
 }
 
 int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s) {
     MC_TRY(union_find_init(w.par, g.n, s));
-    if (g.arcs > 0) { ++::mc::g_launches; k_cc_union<<<grid_for(g.arcs), kThreads, 0, s>>>(g, w.par); }
+    if (g.arcs > 0) {
+        int *giant = reinterpret_cast<int *>(&w.st->count2);
+        ++::mc::g_launches; k_cc_sample<<<grid_for((i64)g.n * kCcSample), kThreads, 0, s>>>(g, w.par);
+        ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n);
+        ++::mc::g_launches; k_cc_giant<<<1, kCcProbe, 0, s>>>(w.root, g.n, giant);
+        ++::mc::g_launches; k_cc_finish<<<grid_for((i64)g.n * 32), kThreads, 0, s>>>(g, w.root, giant, w.par);
+    }
     ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
     MC_TRY(exclusive_scan_i32(w.cnt, w.lab, g.n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));

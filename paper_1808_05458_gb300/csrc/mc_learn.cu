@@ -493,6 +493,7 @@ int proposer_create(Proposer **out, const float *init) {
 void proposer_destroy(Proposer *p) {
     if (!p) return;
     void *ps[] = {p->P, p->M, p->V, p->grad, p->WT, p->Wn, p->acc, p->X, p->Z, p->S, p->dH, p->dG, p->dX, p->Hb, p->Gb, p->dZb};
+    cudaDeviceSynchronize();  // no stream may still use the buffers
     for (void *q : ps) dev_free(q, nullptr);
     delete p;
 }

@@ -22,19 +22,36 @@ void set_error_detail(const char *msg) { g_detail = msg; }
 const std::string &error_detail() { return g_detail; }
 
 // ------------------------------------------------------------- allocation --
-int dev_alloc(void **p, size_t bytes, cudaStream_t) {
-    cudaError_t e = cudaMalloc(p, bytes);
+// Stream-ordered allocations from the device's default pool, which keeps
+// freed memory for reuse (release threshold raised once per device): graphs
+// created and destroyed in a loop then allocate without device-wide syncs.
+static void retain_pool_memory() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long keep = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    (void)cudaGetLastError();
+    done[dev] = true;
+}
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    retain_pool_memory();
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         *p = nullptr;
-        set_cuda_error(e, "cudaMalloc");
+        set_cuda_error(e, "cudaMallocAsync");
         return e == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA;
     }
     return MC_OK;
 }
 
-void dev_free(void *p, cudaStream_t) {
-    if (p) cudaFree(p);
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
 }
 
 int num_sms() {

@@ -205,6 +205,39 @@ def test_disconnected_graph(mc):
     assert res.lam == 0 and oracle.cut_weight(*g, side) == 0 and side[0] == 0 and side.sum() == 4
 
 
+def _disjoint_union(parts):
+    rps, cols, ws, off, base = [np.zeros(1, np.int64)], [], [], 0, 0
+    for rp, col, w in parts:
+        rps.append(rp[1:].astype(np.int64) + base)
+        cols.append(col.astype(np.int64) + off)
+        ws.append(w)
+        off += len(rp) - 1
+        base += len(col)
+    return (np.concatenate(rps).astype(np.int32), np.concatenate(cols).astype(np.int32),
+            np.concatenate(ws).astype(np.int32))
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(tail_vertices=-1), dict(bound=1), dict(pr_level=0)])
+def test_disconnected_components_side(mc, opts):
+    # lambda = 0 is reached by the exact loop itself; the side is every
+    # component but vertex 0's
+    parts = [graphgen.random_connected(300, 900, seed=1, wmax=5), graphgen.random_connected(500, 2000, seed=2),
+             graphgen.random_connected(50, 100, seed=3, wmax=9), graphgen.complete(40, 3)]
+    g = _disjoint_union(parts)
+    sizes = [len(p[0]) - 1 for p in parts]
+    with mc.Graph(*g) as G:
+        res = G.min_cut(mc.options(**opts))
+    side = res.side(len(g[0]) - 1)
+    assert res.lam == 0 and oracle.cut_weight(*g, side) == 0
+    assert (side[:sizes[0]] == 0).all() and (side[sizes[0]:] == 1).all()
+    # an isolated vertex: delta = 0 from the start
+    g2 = _disjoint_union([parts[0], (np.zeros(2, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))])
+    with mc.Graph(*g2) as G:
+        res = G.min_cut(mc.options(**opts))
+    side = res.side(len(g2[0]) - 1)
+    assert res.lam == 0 and side.sum() == 1 and side[-1] == 1
+
+
 def test_tree_and_path(mc):
     for seed in range(5):
         g = graphgen.random_tree(3000, seed)
