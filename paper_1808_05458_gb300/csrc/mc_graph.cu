@@ -177,22 +177,30 @@ k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs, cons
                     c = e.y;
                 }
             }
-            // runs of equal keys among the warp's lanes: sum toward the first
+            // runs of equal keys among the warp's lanes: saturating sums
+            // (both terms <= cap < 2^31, so the u32 add cannot wrap) toward
+            // the run's first lane; a lane takes lane + o's partial sum when
+            // no run starts in (lane, lane + o]
             const u64 kp = __shfl_up_sync(0xffffffffu, kk, 1);
             const bool head = lane == 0 || kp != kk;
             const unsigned hm = __ballot_sync(0xffffffffu, head);
-            const int run = __popc(hm & ((2u << lane) - 1u));
+            const unsigned after = lane == 31 ? 0u : hm >> (lane + 1);
+            bool wide = c > cap;
+            unsigned sv = (unsigned)(c > cap ? cap : c);
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const long long t = __shfl_down_sync(0xffffffffu, c, o);
-                const int ro = __shfl_down_sync(0xffffffffu, run, o);
-                if (lane + o < 32 && ro == run) c += t;
+                const unsigned t = __shfl_down_sync(0xffffffffu, sv, o);
+                if (lane + o < 32 && (after & ((1u << o) - 1u)) == 0) {
+                    const unsigned x = sv + t;
+                    wide |= x > (unsigned)cap;
+                    sv = x > (unsigned)cap ? (unsigned)cap : x;
+                }
             }
             key[k] = ~0ULL;
             if (head && kk != ~0ULL) {
-                if (c > (long long)kInt32Max && clamp > (i64)kInt32Max) atomicOr(err, kErrOverflow);
+                if (wide && clamp > (i64)kInt32Max) atomicOr(err, kErrOverflow);
                 key[k] = kk;
-                val[k] = (int)(c > cap ? cap : c);
+                val[k] = (int)sv;
                 ++cnt;
             }
         }

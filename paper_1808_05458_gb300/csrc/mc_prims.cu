@@ -180,49 +180,26 @@ int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tm
 // LSD radix sort, 8-bit digits.  Per pass: (1) per-tile digit histograms,
 // (2) one exclusive scan over the digit-major histogram matrix gives every
 // (digit, tile) its output offset, (3) each tile ranks its keys stably with
-// per-bit warp ballots, reorders them in shared memory and writes each digit's
+// warp match/ballot, reorders them in shared memory and writes each digit's
 // run contiguously.
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 12;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 3072
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048
 constexpr int kRsWarps = kRsThreads / 32;
 
-// lanes of the warp holding the same 8-bit digit: one ballot per digit bit
-__device__ __forceinline__ unsigned digit_peers(int d) {
-    unsigned peers = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1);
-        peers &= ((d >> b) & 1) ? m : ~m;
-    }
-    return peers;
-}
-
-// per-warp histograms; the lowest lane of each group of equal digits adds
-// the group's size (keys in emitted order share high digits in long runs)
-__global__ void __launch_bounds__(kRsThreads)
-k_rs_hist(const u64 *__restrict__ keys, i64 n, int shift, int ntiles, int *__restrict__ hist) {
-    __shared__ int h[kRsWarps][256];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 256 / 32; ++k) h[wid][k * 32 + lane] = 0;
-    __syncwarp();
-    const i64 base = (i64)blockIdx.x * kRsTile + wid * (kRsItems * 32);
-    const unsigned lt_mask = (1u << lane) - 1u;
+__global__ void k_rs_hist(const u64 *__restrict__ keys, i64 n, int shift, int ntiles,
+                          int *__restrict__ hist) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    i64 base = (i64)blockIdx.x * kRsTile;
 #pragma unroll
     for (int k = 0; k < kRsItems; ++k) {
-        const i64 i = base + k * 32 + lane;
-        const bool ok = i < n;
-        const int d = ok ? (int)((keys[i] >> shift) & 255) : 0;
-        const unsigned peers = digit_peers(d) & __ballot_sync(0xffffffffu, ok);
-        if (ok && (peers & lt_mask) == 0) h[wid][d] += __popc(peers);
-        __syncwarp();
+        i64 i = base + (i64)k * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 255)], 1);
     }
     __syncthreads();
-    int t = 0;
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) t += h[w][threadIdx.x];
-    hist[(i64)threadIdx.x * ntiles + blockIdx.x] = t;
+    hist[(i64)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(kRsThreads)
@@ -256,7 +233,7 @@ k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__re
     }
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
-        unsigned peers = digit_peers(dig[j]);
+        unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
         int before = __popc(peers & lt_mask);
         int base = wcnt[wid][dig[j]];
         __syncwarp();
