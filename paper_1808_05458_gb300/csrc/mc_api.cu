@@ -342,7 +342,9 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         }
         if (unions == 0) {
             const i64 lam_before = lam;
-            MC_TRY(capforest_full(cur, w, cfg, s));
+            ScanConfig cf = cfg;
+            cf.lam_hint = lam;
+            MC_TRY(capforest_full(cur, w, cf, s));
             MC_TRY(status_read(w, s));
             const Status st = *w.h_st;
             S.scanned_arcs += st.scanned_arcs;

@@ -321,13 +321,13 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
         q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.eslot; q.enext = sm.enext;
         q.top = &sm.top; q.cap = SN + SN / 2; q.C = C; q.coarse = C + 1 > kBNB; q.fifo = fifo != 0;
         DenseTable tab{r, n};
-        scan_one<DenseTable, BucketQ<unsigned short, kBNB>>(A, tab, q, start, 1, cnt);
+        scan_one<DenseTable, BucketQ<unsigned short, kBNB>, false, true>(A, tab, q, start, 1, cnt);
     } else {
         BucketQ<int, kBNB> q;
         q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = S.eslot; q.enext = S.enext;
         q.top = &sm.top; q.cap = (int)(arcs + 2); q.C = C; q.coarse = C + 1 > kBNB; q.fifo = fifo != 0;
         DenseTable tab{r, 0};
-        scan_one<DenseTable, BucketQ<int, kBNB>>(A, tab, q, start, 1, cnt);
+        scan_one<DenseTable, BucketQ<int, kBNB>, false, true>(A, tab, q, start, 1, cnt);
     }
     __syncwarp();
 }
@@ -529,12 +529,17 @@ struct TailIn {
     u64 seed;
     int pr_level, fifo;
     Status *out;  // out->lam = the minimum found, out->err
+    u32 *bits_out;  // if set: the side bitmap (n bits) is copied here
 };
 
-// one warp: copy the small graph into its scratch, then Alg. 2's rounds
+// one warp: copy the small graph into its scratch, then Alg. 2's rounds.
+// SMEM_SCRATCH: the whole scratch (graph copies included) lives in dynamic
+// shared memory, so every access of the rounds is on-chip.
+template <int SN, bool SMEM_SCRATCH>
 __global__ void __launch_bounds__(32) k_tail(TailIn T) {
-    __shared__ WarpSmem<kTailSN> sm;
-    Scratch S = scratch_of(T.scratch, T.L);
+    __shared__ WarpSmem<SN> sm;
+    extern __shared__ __align__(256) unsigned char tail_smem[];
+    Scratch S = scratch_of(SMEM_SCRATCH ? tail_smem : T.scratch, T.L);
     const int lane = lane_id();
     const int n = T.g.n;
     const long long arcs = T.g.arcs;
@@ -544,7 +549,9 @@ __global__ void __launch_bounds__(32) k_tail(TailIn T) {
     __syncwarp();
     long long lam = T.lam;
     int err = 0, ovf = 0;
-    exact_rounds<kTailSN>(S, sm, n, arcs, lam, err, ovf, T.seed, 0x7A11ULL, T.pr_level, T.fifo);
+    exact_rounds<SN>(S, sm, n, arcs, lam, err, ovf, T.seed, 0x7A11ULL, T.pr_level, T.fifo);
+    if (T.bits_out && lam < T.lam)
+        for (int i = lane; i < (n + 31) / 32; i += 32) T.bits_out[i] = S.best[i];
     if (lane == 0) {
         T.out->lam = lam;
         T.out->err = err;
@@ -722,17 +729,26 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
     return MC_OK;
 }
 
+// graphs up to kTailSmemN vertices and kTailSmemArcs arcs run with the whole
+// scratch in shared memory
+constexpr int kTailSmemN = 256;
+constexpr int kTailSmemArcs = 4096;
+constexpr int kTailSmemSN = 256;
+
 int tail_solve(const DevGraph &g, Work &w, int limit, long long *lam, u64 seed, int pr_level, int fifo,
                int n0, cudaStream_t s) {
     if (limit > 4096) limit = 4096;
     if (g.n > limit || g.arcs > 64LL * limit || g.n < 2) return MC_EINVAL;
-    const Layout L = make_layout(limit, 64LL * limit);
-    if (w.tail_bytes < L.bytes) {
+    const bool on_chip = g.n <= kTailSmemN && g.arcs <= kTailSmemArcs;
+    const Layout L = on_chip ? make_layout(kTailSmemN, kTailSmemArcs) : make_layout(limit, 64LL * limit);
+    // the side bitmap is read back from global memory in both cases
+    const size_t need = on_chip ? al(4 * ((size_t)kTailSmemN / 32 + 2)) : L.bytes;
+    if (w.tail_bytes < need || !w.tail) {
         dev_free(w.tail, s);
         w.tail = nullptr;
         w.tail_bytes = 0;
-        MC_TRY(dev_alloc(reinterpret_cast<void **>(&w.tail), L.bytes, s));
-        w.tail_bytes = L.bytes;
+        MC_TRY(dev_alloc(reinterpret_cast<void **>(&w.tail), need, s));
+        w.tail_bytes = need;
     }
     TailIn T;
     T.g = g;
@@ -743,7 +759,18 @@ int tail_solve(const DevGraph &g, Work &w, int limit, long long *lam, u64 seed, 
     T.pr_level = pr_level;
     T.fifo = fifo;
     T.out = w.st;
-    ++::mc::g_launches; k_tail<<<1, 32, 0, s>>>(T);
+    T.bits_out = on_chip ? reinterpret_cast<u32 *>(w.tail) : nullptr;
+    if (on_chip) {
+        static bool attr = false;
+        if (!attr) {
+            MC_CUDA(cudaFuncSetAttribute(k_tail<kTailSmemSN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.bytes));
+            attr = true;
+        }
+        ++::mc::g_launches; k_tail<kTailSmemSN, true><<<1, 32, L.bytes, s>>>(T);
+    } else {
+        ++::mc::g_launches; k_tail<kTailSN, false><<<1, 32, 0, s>>>(T);
+    }
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(w, s));
     if (w.h_st->err) {
@@ -751,7 +778,9 @@ int tail_solve(const DevGraph &g, Work &w, int limit, long long *lam, u64 seed, 
         return w.h_st->err;
     }
     if (w.h_st->lam < *lam) {
-        MC_TRY(side_from_bits(w, n0, reinterpret_cast<const u32 *>(w.tail + L.best), s));
+        const u32 *bits = on_chip ? reinterpret_cast<const u32 *>(w.tail)
+                                  : reinterpret_cast<const u32 *>(w.tail + L.best);
+        MC_TRY(side_from_bits(w, n0, bits, s));
         *lam = w.h_st->lam;
     }
     return MC_OK;

@@ -175,7 +175,8 @@ k_capforest_full(ScanArgs A, int start, int *r, int *eslot, int *enext, int pool
     Counters cnt;
     int sid = 1;
     if (lane == 0) atomicAdd(&A.st->scan_ids, 1);
-    scan_one<DenseTable, BucketQ<int, kFullNB>>(A, tab, q, start, sid, cnt);
+    scan_one<DenseTable, BucketQ<int, kFullNB>, false, true>(A, tab, q, start, sid, cnt);
+    if (lane == 0 && A.pairs) A.st->count = cnt.npairs;
     long long un = cnt.unions;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
@@ -185,6 +186,90 @@ k_capforest_full(ScanArgs A, int start, int *r, int *eslot, int *enext, int pool
         atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)cnt.verts);
         atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), 1ULL);
     }
+}
+
+// full scan of a small graph with a small cap: the r-values, the row
+// offsets, the degrees and a dense bitmap queue all in shared memory
+constexpr int kFullBitN = 8192;
+
+__host__ __device__ inline size_t full_bit_smem(int n, int nbk) {
+    const size_t W = ((size_t)n + 31) / 32;
+    size_t b = 4 * (size_t)n + 4 * ((size_t)n + 1);
+    b = (b + 7) / 8 * 8;
+    return b + 8 * (size_t)n + 4 * (size_t)nbk * W + 4 * (size_t)nbk;
+}
+
+template <int NBK>
+__global__ void __launch_bounds__(32)
+k_capforest_full_bit(ScanArgs A, int start) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int lane = threadIdx.x & 31;
+    const int n = A.g.n;
+    const int W = (n + 31) / 32;
+    int *r = reinterpret_cast<int *>(fsm);
+    int *rp = r + n;
+    size_t off = 4 * (size_t)n + 4 * ((size_t)n + 1);
+    off = (off + 7) / 8 * 8;
+    long long *deg = reinterpret_cast<long long *>(fsm + off);
+    u32 *bits = reinterpret_cast<u32 *>(deg + n);
+    int *cnt = reinterpret_cast<int *>(bits + (size_t)NBK * W);
+    for (int v = lane; v < n; v += 32) { r[v] = 0; rp[v] = A.g.rp[v]; deg[v] = A.g.deg[v]; }
+    if (lane == 0) rp[n] = A.g.rp[n];
+    for (int i = lane; i < NBK * W; i += 32) bits[i] = 0;
+    for (int i = lane; i < NBK; i += 32) cnt[i] = 0;
+    __syncwarp();
+    const long long L = ld_volatile_i64(&A.st->lam);
+    if (L <= 0) return;
+    DenseBitQ<NBK> q;
+    q.bits = bits;
+    q.cnt = cnt;
+    q.W = W;
+    q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
+    DenseTable tab{r, 0};
+    ScanArgs B = A;
+    B.g.rp = rp;
+    B.g.deg = deg;
+    Counters c;
+    if (lane == 0) atomicAdd(&A.st->scan_ids, 1);
+    scan_one<DenseTable, DenseBitQ<NBK>, false, true>(B, tab, q, start, 1, c);
+    if (lane == 0) A.st->count = c.npairs;
+    long long un = c.unions;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), (unsigned long long)un);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)c.arcs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)c.verts);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), 1ULL);
+    }
+}
+
+template <int NBK>
+static int launch_full_bit(const ScanArgs &A, int start, cudaStream_t s) {
+    const size_t smem = full_bit_smem(A.g.n, NBK);
+    static bool attr = false;
+    if (!attr) {
+        MC_CUDA(cudaFuncSetAttribute(k_capforest_full_bit<NBK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)full_bit_smem(kFullBitN, 64)));
+        attr = true;
+    }
+    ++::mc::g_launches; k_capforest_full_bit<NBK><<<1, 32, smem, s>>>(A, start);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+// the unions a lone scan recorded (st->count pairs), counted into st->unions
+__global__ void k_apply_pairs(const u64 *__restrict__ pairs, Status *st, int *par) {
+    const long long np = st->count;
+    long long un = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x) {
+        const u64 p = pairs[i];
+        if (uf_union(par, (int)(p >> 32), (int)(p & 0xFFFFFFFFu))) ++un;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+    if ((threadIdx.x & 31) == 0 && un)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&st->unions), (unsigned long long)un);
 }
 
 // smallest scan id whose best alpha equals lambda-hat
@@ -340,7 +425,21 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
     const i64 pool = g.arcs + 2;
     int *eslot = reinterpret_cast<int *>(w.fb_pool);
     int *enext = eslot + pool;
-    ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, w.fb_r, eslot, enext, (int)pool, cfg.pq_fifo);
+    // the lone scan records its unions (at most one per arc) in the radix
+    // key buffer; one parallel pass applies them
+    A.pairs = w.keysA;
+    MC_CUDA(cudaMemsetAsync(&w.st->count, 0, sizeof(w.st->count), s));
+    if (!cfg.pq_fifo && cfg.lam_hint > 0 && cfg.lam_hint < 64 && g.n <= kFullBitN) {
+        MC_TRY(cfg.lam_hint < 16 ? launch_full_bit<16>(A, start, s) : launch_full_bit<64>(A, start, s));
+    } else {
+        ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, w.fb_r, eslot, enext, (int)pool, cfg.pq_fifo);
+    }
+    {
+        int blocks = (int)((g.arcs + 255) / 256);
+        if (blocks > num_sms() * 4) blocks = num_sms() * 4;
+        if (blocks < 1) blocks = 1;
+        ++::mc::g_launches; k_apply_pairs<<<blocks, 256, 0, s>>>(w.keysA, w.st, w.par);
+    }
     ++::mc::g_launches; k_best_scan<<<1, 32, 0, s>>>(w.rec_alpha, w.rec_len, w.st);
     ++::mc::g_launches; k_best_len<<<1, 1, 0, s>>>(w.rec_len, w.st);
     MC_CUDA(cudaGetLastError());

@@ -45,8 +45,16 @@ __device__ __forceinline__ void warp_argmax(long long &w, int &l) {
 struct LpSmem {
     int key[kLpHash];
     unsigned long long val[kLpHash];
+    unsigned long long sum[32];  // per-lane label weights of a short row
+    short used[kLpSmemRow];      // hash slots a longer row filled
+    int nused;
 };
 
+// Each warp takes 32 consecutive vertices at a time: their parities and row
+// bounds come in one coalesced step, vertices outside this half-sweep keep
+// their label, and the warp then works through the active ones.  A row of
+// <= 32 arcs groups equal labels with match_any and adds each group's
+// weights in shared memory at its lowest lane.
 __global__ void __launch_bounds__(kLpWarps * 32)
 k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const int *__restrict__ lin,
           int *__restrict__ lout, u64 seed, int sweep, int half, int *big_list, int *big_count) {
@@ -54,73 +62,84 @@ k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const
     LpSmem &h = sm[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < kLpHash; i += 32) { h.key[i] = -1; h.val[i] = 0; }
+    h.sum[lane] = 0;
+    if (lane == 0) h.nused = 0;
     __syncwarp();
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
-        const int cur = lin[v];
-        if (lp_parity(seed, sweep, v) != half) {
-            if (lane == 0) lout[v] = cur;
-            continue;
-        }
-        const int a0 = rp[v], a1 = rp[v + 1], d = a1 - a0;
-        if (d == 0) {
-            if (lane == 0) lout[v] = cur;
-            continue;
-        }
-        if (d > kLpSmemRow) {  // hub: the block kernel decides
-            if (lane == 0) big_list[atomicAdd(big_count, 1)] = v;
-            continue;
-        }
-        long long bw = -1;
-        int bl = INT_MAX;
-        if (d <= 32) {
-            int lab = -1 - lane;
-            long long wt = 0;
-            if (lane < d) {
-                const int2 e = adj[a0 + lane];
-                lab = lin[e.x];
-                wt = e.y;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
+        const int v = base + lane;
+        int a0 = 0, a1 = 0, cur = 0;
+        bool act = false;
+        if (v < n) {
+            cur = lin[v];
+            a0 = rp[v];
+            a1 = rp[v + 1];
+            act = lp_parity(seed, sweep, v) == half && a1 > a0;
+            if (act && a1 - a0 > kLpSmemRow) {  // hub: the block kernel decides
+                big_list[atomicAdd(big_count, 1)] = v;
+                act = false;
+            } else if (!act) {
+                lout[v] = cur;
             }
-            // total weight of this lane's label over the row (all 32 lanes)
-            long long sum = 0;
-            for (int j = 0; j < 32; ++j) {
-                const int lj = __shfl_sync(0xffffffffu, lab, j);
-                const long long wj = __shfl_sync(0xffffffffu, wt, j);
-                if (lj == lab) sum += wj;
-            }
-            if (lane < d) { bw = sum; bl = lab; }
-        } else {
-            for (int i = a0 + lane; i < a1; i += 32) {
-                const int2 e = adj[i];
-                const int lab = lin[e.x];
-                unsigned hh = ((unsigned)lab * 2654435761u) >> (32 - 10);
-                while (true) {
-                    const int k = atomicCAS(&h.key[hh], -1, lab);
-                    if (k == -1 || k == lab) break;
-                    hh = (hh + 1) & (kLpHash - 1);
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, act);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int u = base + l;
+            const int r0 = __shfl_sync(0xffffffffu, a0, l), r1 = __shfl_sync(0xffffffffu, a1, l);
+            const int d = r1 - r0;
+            long long bw = -1;
+            int bl = INT_MAX;
+            if (d <= 32) {
+                int lab = -1 - lane;
+                int wt = 0;
+                if (lane < d) {
+                    const int2 e = adj[r0 + lane];
+                    lab = lin[e.x];
+                    wt = e.y;
                 }
-                atomicAdd(&h.val[hh], (unsigned long long)e.y);
+                const unsigned peers = __match_any_sync(0xffffffffu, lab);
+                const int lead = __ffs(peers) - 1;
+                if (lane < d) atomicAdd(&h.sum[lead], (unsigned long long)wt);
+                __syncwarp();
+                if (lane < d && lead == lane) { bw = (long long)h.sum[lane]; bl = lab; }
+                __syncwarp();
+                h.sum[lane] = 0;
+            } else {
+                for (int i = r0 + lane; i < r1; i += 32) {
+                    const int2 e = adj[i];
+                    const int lab = lin[e.x];
+                    unsigned hh = ((unsigned)lab * 2654435761u) >> (32 - 10);
+                    while (true) {
+                        const int k = atomicCAS(&h.key[hh], -1, lab);
+                        if (k == -1) { h.used[atomicAdd(&h.nused, 1)] = (short)hh; break; }
+                        if (k == lab) break;
+                        hh = (hh + 1) & (kLpHash - 1);
+                    }
+                    atomicAdd(&h.val[hh], (unsigned long long)e.y);
+                }
+                __syncwarp();
+                // the row's labels sit in the slots it filled (<= d of them);
+                // read them, then clear exactly those
+                const int nu = h.nused;
+                for (int i = lane; i < nu; i += 32) {
+                    const int slot = h.used[i];
+                    const int k = h.key[slot];
+                    if (lp_better((long long)h.val[slot], k, bw, bl)) { bw = (long long)h.val[slot]; bl = k; }
+                }
+                __syncwarp();
+                for (int i = lane; i < nu; i += 32) {
+                    const int slot = h.used[i];
+                    h.key[slot] = -1;
+                    h.val[slot] = 0;
+                }
+                if (lane == 0) h.nused = 0;
+                __syncwarp();
             }
-            __syncwarp();
-            for (int i = lane; i < kLpHash; i += 32) {
-                const int k = h.key[i];
-                if (k >= 0 && lp_better((long long)h.val[i], k, bw, bl)) { bw = (long long)h.val[i]; bl = k; }
-            }
-            __syncwarp();
-            // clear only the slots this row used
-            for (int i = a0 + lane; i < a1; i += 32) {
-                const int lab = lin[adj[i].x];
-                unsigned hh = ((unsigned)lab * 2654435761u) >> (32 - 10);
-                while (h.key[hh] != lab && h.key[hh] != -1) hh = (hh + 1) & (kLpHash - 1);
-                if (h.key[hh] == lab) { h.key[hh] = -2; }
-            }
-            __syncwarp();
-            for (int i = lane; i < kLpHash; i += 32)
-                if (h.key[i] == -2) { h.key[i] = -1; h.val[i] = 0; }
-            __syncwarp();
+            warp_argmax(bw, bl);
+            if (lane == 0) lout[u] = bl;
         }
-        warp_argmax(bw, bl);
-        if (lane == 0) lout[v] = bl;
     }
 }
 

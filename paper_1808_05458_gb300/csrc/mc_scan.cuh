@@ -214,10 +214,15 @@ struct ScanArgs {
     int *rec_len;
     u64 perm_a, perm_b;
     int limit;
+    // a scan running alone may record its unions (x << 32 | y) here instead
+    // of applying them (the scan never reads the union-find, so applying the
+    // list afterwards gives the same partition); nullptr = apply at once
+    u64 *pairs = nullptr;
 };
 
 struct Counters {
     long long arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
+    long long npairs = 0;  // unions recorded in ScanArgs::pairs
 };
 
 // garbage-collect a hash table's queue: rebuild every bucket list from the
@@ -254,8 +259,16 @@ __device__ bool HashTable<HC, SM>::rebuild(Q &q) const {
 }
 
 template <class Q>
+__device__ bool dense_rebuild(const DenseTable &t, Q &q);
+template <class Q>
 __device__ bool DenseTable::rebuild(Q &q) const {
+    return dense_rebuild(*this, q);
+}
+template <class Q>
+__device__ bool dense_rebuild(const DenseTable &t, Q &q) {
     const int lane = threadIdx.x & 31;
+    const int n_rebuild = t.n_rebuild;
+    const int *r = t.r;
     if (n_rebuild <= 0) return false;
     for (int b = lane; b < Q::kNBuckets; b += 32) { q.head[b] = -1; q.tail[b] = -1; }
     for (int b = lane; b < Q::kNBuckets / 32; b += 32) q.bits[b] = 0;
@@ -348,11 +361,83 @@ __device__ __forceinline__ int q_pop(BitQ<HC, NBK> &q, const int *) {
     return s;
 }
 
+// Bitmap bucket queue over a dense slot range [0, n) (full scans of small
+// graphs): bucket b is a bitmap of W = ceil(n / 32) words plus a count, as in
+// BitQ, with W a run-time size; a pop searches the top bucket's words 32 at a
+// time.  Needs C < NBK.
+template <int NBK>
+struct DenseBitQ {
+    u32 *bits;  // NBK x W words
+    int *cnt;   // NBK counts
+    int W;
+    int C;
+    bool coarse = false;
+    __device__ __forceinline__ int bucket(int k) const { return k; }
+};
+template <int NBK>
+__device__ __forceinline__ bool q_changed(const DenseBitQ<NBK> &q, int ko, int kn) {
+    return ko != kn;
+}
+template <int NBK>
+__device__ __forceinline__ bool q_update(DenseBitQ<NBK> &q, bool want, int s, int ko, int kn) {
+    if (want) {
+        const u32 bit = 1u << (s & 31);
+        const int wd = s >> 5;
+        if (ko >= 0) {
+            atomicAnd(&q.bits[ko * q.W + wd], ~bit);
+            atomicSub(&q.cnt[ko], 1);
+        }
+        atomicOr(&q.bits[kn * q.W + wd], bit);
+        atomicAdd(&q.cnt[kn], 1);
+    }
+    __syncwarp();
+    return true;
+}
+template <int NBK>
+__device__ __forceinline__ int q_pop(DenseBitQ<NBK> &q, const int *) {
+    static_assert(NBK <= 64, "dense bitmap queue bounds");
+    const int lane = threadIdx.x & 31;
+    int top = -1;
+#pragma unroll
+    for (int b0 = ((NBK - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
+        const int b = b0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, b < NBK && b <= q.C && q.cnt[b] > 0);
+        if (top < 0 && m) top = b0 + 31 - __clz(m);
+    }
+    if (top < 0) return -1;
+    const u32 *row = q.bits + (size_t)top * q.W;
+    int s = -1;
+    for (int w0 = 0; w0 < q.W && s < 0; w0 += 32) {
+        const u32 word = w0 + lane < q.W ? row[w0 + lane] : 0u;
+        const unsigned m = __ballot_sync(0xffffffffu, word != 0u);
+        if (m) {
+            const int wl = __ffs(m) - 1;
+            const u32 wv = __shfl_sync(0xffffffffu, word, wl);
+            s = (w0 + wl) * 32 + __ffs(wv) - 1;
+        }
+    }
+    __syncwarp();
+    if (lane == 0 && s >= 0) {
+        q.bits[(size_t)top * q.W + (s >> 5)] &= ~(1u << (s & 31));
+        q.cnt[top] -= 1;
+    }
+    __syncwarp();
+    return s;
+}
+template <int NBK>
+__device__ __forceinline__ bool dense_rebuild(const DenseTable &, DenseBitQ<NBK> &) {
+    return true;  // never out of room
+}
+
 // A scan with PRECHECK looks up the owner of every vertex it touches for the
 // first time: a vertex another scan already owns is blacklisted right away
 // (Alg. 1's blacklisting, taken before any of its arcs count, so it never
 // enters this scan's r-values -- Lemma 2 part 3).
-template <class Table, class Q, bool PRECHECK = false>
+//
+// SOLO: the scan runs alone on its graph (a full scan, one warp per graph):
+// every claim succeeds, so T is written without an atomic, and lambda-hat
+// changes only through this scan, so it is kept in a register.
+template <class Table, class Q, bool PRECHECK = false, bool SOLO = false>
 __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt) {
     const int lane = threadIdx.x & 31;
     const int n = A.g.n;
@@ -364,6 +449,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         q_update(q, lane == 0, s, -1, 0);
     }
     long long alpha = 0, best = LLONG_MAX;
+    long long L_solo = SOLO ? ld_volatile_i64(&A.st->lam) : 0;
     int nS = 0, best_len = 0;
     bool alpha_ok = true, stop = false;
     cnt.scans++;
@@ -376,18 +462,21 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         int old = 0;
         if (lane == 0) {
             rv[s] = kDone;
-            old = atomicCAS(&A.T[x], 0, sid);
+            if (SOLO) A.T[x] = sid;
+            else old = atomicCAS(&A.T[x], 0, sid);
         }
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old != 0) {
-            cnt.black++;
-            continue;
+        if (!SOLO) {
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old != 0) {
+                cnt.black++;
+                continue;
+            }
         }
         long long L = 0, dx = 0;
         int a0 = 0, a1 = 0;
         if (lane == 0) {
             A.order[x] = nS;
-            L = ld_volatile_i64(&A.st->lam);
+            L = SOLO ? L_solo : ld_volatile_i64(&A.st->lam);
             a0 = A.g.rp[x];
             a1 = A.g.rp[x + 1];
             dx = A.g.deg[x];
@@ -403,6 +492,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             if (lane == 0) atomicMin(&A.st->lam, alpha);
             if (alpha < best) { best = alpha; best_len = nS; }
             L = alpha;
+            L_solo = alpha;
         }
         cnt.verts++;
         cnt.arcs += a1 - a0;
@@ -420,7 +510,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             // weight is 0 in Lemma 1's lowered graph) and alpha is no longer
             // the cut of S, but the scan goes on over the vertices it holds
             if (__any_sync(0xffffffffu, v && s2 < 0)) alpha_ok = false;
-            bool push = false;
+            bool push = false, join = false;
             int kn = 0, ko = -1;
             if (s2 >= 0) {
                 int r_old = rv[s2];
@@ -433,14 +523,19 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
                     int r_new = sat_add(r_old, c);
                     rv[s2] = r_new;
                     // a certificate q = min(r, C) can only vouch for bounds <= C
-                    if ((long long)r_old < L && L <= (long long)r_new && L <= (long long)C) {
-                        if (uf_union(A.par, x, y)) cnt.unions++;
-                    }
+                    join = (long long)r_old < L && L <= (long long)r_new && L <= (long long)C;
                     const int kold = r_old < C ? r_old : C;
                     kn = r_new < C ? r_new : C;
                     push = r_old == 0 || q_changed(q, kold, kn);
                     ko = r_old == 0 ? -1 : kold;
                 }
+            }
+            if (SOLO && A.pairs) {
+                const unsigned jm = __ballot_sync(0xffffffffu, join);
+                if (join) A.pairs[cnt.npairs + __popc(jm & ((1u << lane) - 1u))] = ((u64)(u32)x << 32) | (u32)y;
+                cnt.npairs += __popc(jm);
+            } else if (join && uf_union(A.par, x, y)) {
+                cnt.unions++;
             }
             // a full pool is rebuilt from the live slots (they already hold
             // this chunk's new keys); a table that cannot rebuild ends the scan
