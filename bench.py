@@ -119,9 +119,10 @@ def kernel_traffic(kernel_name):
         with open(path) as f:
             d = json.load(f)
         ent = d[kernel_name]
-        src = os.path.join(ROOT, ent["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != ent["source_sha256_16"]:
+        h = hashlib.sha256()
+        for src in ent["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        if h.hexdigest()[:16] != ent["sources_sha256_16"]:
             return None
         return ent
     except (OSError, KeyError, ValueError):
