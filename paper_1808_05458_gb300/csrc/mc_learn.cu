@@ -48,11 +48,11 @@ __global__ void k_features(DevGraph g, long long delta, u64 seed, const float *_
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += nw) {
         const int a0 = g.rp[v], a1 = g.rp[v + 1];
-        double sum = 0;
+        long long sum = 0;  // exact; the features themselves are float
         long long mn = LLONG_MAX;
         for (int i = a0 + lane; i < a1; i += 32) {
             const long long du = g.deg[g.adj[i].x];
-            sum += (double)du;
+            sum += du;
             mn = du < mn ? du : mn;
         }
 #pragma unroll
@@ -62,15 +62,15 @@ __global__ void k_features(DevGraph g, long long delta, u64 seed, const float *_
             mn = om < mn ? om : mn;
         }
         const int a = a1 - a0;
-        const double d = (double)g.deg[v];
+        const float d = (float)g.deg[v];
         float x[kF];
         x[0] = 1.f;
-        x[1] = (float)(log1p(d) / 8.0);
-        x[2] = (float)(log1p((double)a) / 8.0);
-        const double rel = delta > 0 ? d / (double)delta - 1.0 : 0.0;
-        x[3] = (float)((rel < 8.0 ? rel : 8.0) / 8.0);
-        x[4] = (float)(log1p(a > 0 ? sum / a : 0.0) / 8.0);
-        x[5] = (float)(log1p(a > 0 ? (double)mn : 0.0) / 8.0);
+        x[1] = log1pf(d) / 8.f;
+        x[2] = log1pf((float)a) / 8.f;
+        const float rel = delta > 0 ? d / (float)delta - 1.f : 0.f;
+        x[3] = (rel < 8.f ? rel : 8.f) / 8.f;
+        x[4] = log1pf(a > 0 ? (float)sum / (float)a : 0.f) / 8.f;
+        x[5] = log1pf(a > 0 ? (float)mn : 0.f) / 8.f;
         const u64 h = splitmix64(seed ^ splitmix64((u64)(unsigned)v));
         x[6] = 2.f * u01s(h) - 1.f;
         x[7] = 2.f * u01s(splitmix64(h)) - 1.f;
@@ -368,7 +368,7 @@ __global__ void k_score_keys(const float *__restrict__ S, int n, u64 *keys, int 
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         unsigned b = __float_as_uint(S[v]);
         b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // order-preserving
-        keys[v] = ((u64)b << 32) | (u64)(unsigned)v;
+        keys[v] = (u64)b;  // the stable sort keeps equal scores in vertex order
         vals[v] = v;
     }
 }
@@ -387,56 +387,118 @@ __global__ void k_sweep_terms(DevGraph g, const int *__restrict__ rank, long lon
         term[rv] = t;
     }
 }
-// inclusive prefix over term (single block) -> min over prefixes 1..n-1
-__global__ void k_sweep_min(const long long *__restrict__ term, int n, long long *best, int *best_k) {
-    __shared__ long long carry;
-    __shared__ long long wb[32];
-    __shared__ int wk[32];
-    if (threadIdx.x == 0) carry = 0;
+// Minimum over the prefix sums P(k) = term[0] + ... + term[k-1], k = 1..n-1
+// (the cut between the k lowest-ranked vertices and the rest), smallest k
+// on ties.  Tiles of kSwTile terms: tile sums, one scan of the tile sums,
+// per-tile minima, one final reduction.
+constexpr int kSwThreads = 256, kSwItems = 8, kSwTile = kSwThreads * kSwItems;
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *total) {
+    __shared__ long long ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) ws[wid] = inc;
     __syncthreads();
-    long long mb = LLONG_MAX;
-    int mk = 0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        long long v = i < n ? term[i] : 0;
+    if (wid == 0) {
+        const long long x = lane < nwarp ? ws[lane] : 0;
+        long long xs = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
+            const long long t = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += t;
         }
-        if (lane == 31) wb[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            long long x = lane < (int)(blockDim.x >> 5) ? wb[lane] : 0;
-            long long xs = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long t = __shfl_up_sync(0xffffffffu, xs, o);
-                if (lane >= o) xs += t;
-            }
-            if (lane < (int)(blockDim.x >> 5)) wb[lane] = xs - x;
-        }
-        __syncthreads();
-        const long long pre = carry + wb[wid] + v;  // cut of the first i+1 vertices
-        if (i < n - 1 && (pre < mb || (pre == mb && i + 1 < mk))) { mb = pre; mk = i + 1; }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = pre;
-        __syncthreads();
+        if (lane < nwarp) ws[lane] = xs - x;
+        if (lane == nwarp - 1) *total = xs;
     }
+    __syncthreads();
+    const long long r = ws[wid] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void better_cut(long long &mb, int &mk, long long ob, int ok) {
+    if (ob < mb || (ob == mb && ok < mk)) { mb = ob; mk = ok; }
+}
+
+__device__ void block_min_cut(long long &mb, int &mk) {
+    __shared__ long long wb[32];
+    __shared__ int wk[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long ob = __shfl_xor_sync(0xffffffffu, mb, o);
-        const int ok = __shfl_xor_sync(0xffffffffu, mk, o);
-        if (ob < mb || (ob == mb && ok < mk)) { mb = ob; mk = ok; }
-    }
+    for (int o = 16; o > 0; o >>= 1)
+        better_cut(mb, mk, __shfl_xor_sync(0xffffffffu, mb, o), __shfl_xor_sync(0xffffffffu, mk, o));
     if (lane == 0) { wb[wid] = mb; wk[wid] = mk; }
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) better_cut(mb, mk, wb[k], wk[k]);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSwThreads) k_sw_tile_sum(const long long *__restrict__ term, int n,
+                                                            long long *tsum) {
+    __shared__ long long total;
+    const long long base = (long long)blockIdx.x * kSwTile + (long long)threadIdx.x * kSwItems;
+    long long v = 0;
+#pragma unroll
+    for (int k = 0; k < kSwItems; ++k)
+        if (base + k < n) v += term[base + k];
+    block_excl_scan_ll(v, &total);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = total;
+}
+
+// exclusive scan of the T tile sums in place (one block)
+__global__ void k_sw_tile_scan(long long *tsum, int T) {
+    __shared__ long long total;
+    long long carry = 0;
+    for (int base = 0; base < T; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const long long v = i < T ? tsum[i] : 0;
+        const long long ex = block_excl_scan_ll(v, &total);
+        if (i < T) tsum[i] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSwThreads) k_sw_tile_min(const long long *__restrict__ term, int n,
+                                                            const long long *__restrict__ toff,
+                                                            long long *bmin, int *bk) {
+    __shared__ long long total;
+    const long long base = (long long)blockIdx.x * kSwTile + (long long)threadIdx.x * kSwItems;
+    long long t[kSwItems];
+    long long v = 0;
+#pragma unroll
+    for (int k = 0; k < kSwItems; ++k) {
+        t[k] = base + k < n ? term[base + k] : 0;
+        v += t[k];
+    }
+    long long pre = toff[blockIdx.x] + block_excl_scan_ll(v, &total);
+    long long mb = LLONG_MAX;
+    int mk = INT_MAX;
+#pragma unroll
+    for (int k = 0; k < kSwItems; ++k) {
+        pre += t[k];  // cut of the first i + 1 vertices
+        const long long i = base + k;
+        if (i < n - 1) better_cut(mb, mk, pre, (int)(i + 1));
+    }
+    block_min_cut(mb, mk);
+    if (threadIdx.x == 0) { bmin[blockIdx.x] = mb; bk[blockIdx.x] = mk; }
+}
+
+__global__ void k_sw_final(const long long *__restrict__ bmin, const int *__restrict__ bk, int T,
+                           long long *best, int *best_k) {
+    long long mb = LLONG_MAX;
+    int mk = INT_MAX;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) better_cut(mb, mk, bmin[i], bk[i]);
+    block_min_cut(mb, mk);
     if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-            if (wb[k] < mb || (wb[k] == mb && wk[k] < mk)) { mb = wb[k]; mk = wk[k]; }
         *best = mb;
-        *best_k = mk;
+        *best_k = mk == INT_MAX ? 0 : mk;
     }
 }
 
@@ -598,14 +660,22 @@ int proposer_sweep(Proposer &p, const DevGraph &g, Work &w, long long *cut, int 
     const int tb = blocks_for(n, 256);
     ++::mc::g_launches; k_score_keys<<<tb, 256, 0, s>>>(p.S, n, w.keysA, w.valsA);
     bool in_b = false;
-    MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, n, 64, w.radix_tmp, w.scan_tmp, &in_b, s));
+    MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, n, 32, w.radix_tmp, w.scan_tmp, &in_b, s));
     const int *order = in_b ? w.valsB : w.valsA;
     ++::mc::g_launches; k_rank<<<tb, 256, 0, s>>>(order, n, w.root);
     long long *term = reinterpret_cast<long long *>(in_b ? w.keysA : w.keysB);
     ++::mc::g_launches; k_sweep_terms<<<tb, 256, 0, s>>>(g, w.root, term);
     long long *d_best = reinterpret_cast<long long *>(&w.st->count);
     int *d_k = &w.st->best_len;
-    ++::mc::g_launches; k_sweep_min<<<1, 1024, 0, s>>>(term, n, d_best, d_k);
+    // tile scratch in the sorted-key buffer (free once the ranks are out)
+    const int T = (n + kSwTile - 1) / kSwTile;
+    long long *tsum = reinterpret_cast<long long *>(in_b ? w.keysB : w.keysA);
+    long long *bmin = tsum + T;
+    int *bk = reinterpret_cast<int *>(bmin + T);
+    ++::mc::g_launches; k_sw_tile_sum<<<T, kSwThreads, 0, s>>>(term, n, tsum);
+    ++::mc::g_launches; k_sw_tile_scan<<<1, 1024, 0, s>>>(tsum, T);
+    ++::mc::g_launches; k_sw_tile_min<<<T, kSwThreads, 0, s>>>(term, n, tsum, bmin, bk);
+    ++::mc::g_launches; k_sw_final<<<1, 1024, 0, s>>>(bmin, bk, T, d_best, d_k);
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(w, s));
     *cut = w.h_st->count;
