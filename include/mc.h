@@ -69,7 +69,8 @@ typedef struct mc_options {
                                 PR1/PR2 run every round, PR3/PR4 in rounds whose
                                 scans unite < n/4 vertices; default 4           */
     int32_t scans_per_round; /* concurrent CAPFOREST warps, 0 = auto           */
-    int32_t region_budget;   /* max vertices touched by one scan, 0 = auto     */
+    int32_t region_budget;   /* max vertices touched by one scan, 0 = auto
+                                (192; 320 on graphs with >= 48 arcs/vertex)  */
     int32_t lp_iters;        /* label-propagation sweeps for MC_BOUND_LP, 0=auto*/
     uint64_t seed;           /* start vertices / LP parity                      */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = the graph's own */
