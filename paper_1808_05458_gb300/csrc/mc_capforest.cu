@@ -373,8 +373,27 @@ static ScanArgs make_args(const DevGraph &g, Work &w, const ScanConfig &cfg) {
     return A;
 }
 
+// Hubs (rows longer than kHubArcs) are never scanned by the concurrent
+// scans: their owner entry starts at -1, so a pop of a hub fails its claim
+// and the hub is passed over, while as a neighbour it is still touched and
+// can be united when its r-value crosses lambda-hat.  A scan that passes
+// over a vertex is a capped scan of the graph without it, whose connectivities
+// are no larger (the unions stay valid), and alpha stays the cut of the
+// scanned set S.  One warp would otherwise walk a hub row of 10^5 arcs alone.
+constexpr int kHubArcs = 4096;
+
+__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        T[v] = rp[v + 1] - rp[v] > kHubArcs ? -1 : 0;
+}
+
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s) {
-    MC_CUDA(cudaMemsetAsync(w.T, 0, sizeof(int) * (size_t)g.n, s));
+    {
+        int blocks = (g.n + 255) / 256;
+        if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+        if (blocks < 1) blocks = 1;
+        ++::mc::g_launches; k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T);
+    }
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
     // default region budget, measured on RHG: 192 touched vertices per scan

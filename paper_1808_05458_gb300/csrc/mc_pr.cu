@@ -18,9 +18,9 @@
 // of such vertices at most once and slides along it at equal weight, and a
 // path's k inner vertices close at most k of its k+1 edges.
 //
-// One thread per arc (u < v).  PR3/PR4 walk the shorter of the two sorted
-// rows and binary-search each neighbour in the longer one, only when the
-// shorter row has at most `budget` arcs (all rows when budget < 0).
+// PR1/PR2: one thread per arc (u < v).  PR3/PR4: one warp per vertex (see
+// k_pr34), only on edges whose shorter row has at most `budget` arcs (all
+// edges when budget < 0).
 #include "mc_internal.cuh"
 
 namespace mc {
@@ -36,7 +36,8 @@ __device__ __forceinline__ int row_weight(const int *rp, const int2 *adj, int v,
     return 0;
 }
 
-__global__ void k_pr(const DevGraph g, int *par, long long lam, int lo, int level, int budget,
+// PR1/PR2 (lo <= 2) on every arc u < v, and the degree-2 tie rule
+__global__ void k_pr(const DevGraph g, int *par, long long lam, int lo, int level,
                      unsigned long long *unions) {
     long long local = 0;
     for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x) {
@@ -48,27 +49,6 @@ __global__ void k_pr(const DevGraph g, int *par, long long lam, int lo, int leve
         const long long du = g.deg[u], dv = g.deg[v];
         bool ok = (lo <= 1 && level >= 1 && c >= lam) ||
                   (lo <= 2 && level >= 2 && 2 * c > (du < dv ? du : dv));
-        if (!ok && level >= 3) {
-            const int lu = g.rp[u + 1] - g.rp[u], lv = g.rp[v + 1] - g.rp[v];
-            const int a = lu <= lv ? u : v, b = lu <= lv ? v : u;
-            const int la = lu <= lv ? lu : lv;
-            if (budget < 0 || la <= budget) {
-                long long pr4 = c;
-                for (int k = g.rp[a]; k < g.rp[a + 1] && !ok; ++k) {
-                    const int2 x = g.adj[k];
-                    if (x.x == b) continue;
-                    const int cb = row_weight(g.rp, g.adj, b, x.x);
-                    if (cb == 0) continue;
-                    // weights to the common neighbour from u and from v
-                    const long long cuw = (a == u) ? x.y : cb;
-                    const long long cvw = (a == u) ? cb : x.y;
-                    if (2 * (c + cuw) > du && 2 * (c + cvw) > dv) ok = true;
-                    pr4 += cuw < cvw ? cuw : cvw;
-                    if (level >= 4 && pr4 >= lam) ok = true;  // early exit
-                }
-                if (!ok && level >= 4 && pr4 >= lam) ok = true;
-            }
-        }
         if (ok && uf_union(par, u, v)) ++local;
     }
     // degree-2 tie rule: a vertex with exactly two neighbours of equal weight
@@ -84,14 +64,95 @@ __global__ void k_pr(const DevGraph g, int *par, long long lam, int lo, int leve
     if (local) atomicAdd(unions, (unsigned long long)local);
 }
 
+// PR3/PR4, one warp per vertex u.  Edge {u, v} belongs to the endpoint with
+// the shorter row (ties: the smaller id), and only when that row has at most
+// `budget` arcs (any length when budget < 0): the warp's lanes take u's
+// neighbours w, binary-search c(v, w) in v's sorted row, and the warp sums
+// PR4's minima and ORs PR3's condition.  Work per vertex grows with the
+// square of its own (short) row, so hubs cost little.  Edges that pass
+// PR1/PR2 in the same call (lo <= 2) are left to k_pr.
+constexpr int kPrWarps = 8;
+
+__device__ __forceinline__ int find_in_global(const int2 *row, int len, int x) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int2 e = row[mid];
+        if (e.x == x) return e.y;
+        if (e.x < x) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(kPrWarps * 32)
+k_pr34(const DevGraph g, int *par, long long lam, int lo, int level, int budget, unsigned long long *unions) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    long long local = 0;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < g.n; u += nw) {
+        const int u0 = g.rp[u], u1 = g.rp[u + 1], lu = u1 - u0;
+        if (lu == 0 || (budget >= 0 && lu > budget)) continue;
+        const long long du = g.deg[u];
+        for (int i0 = u0; i0 < u1; i0 += 32) {
+            const int i = i0 + lane;
+            bool cand = false;
+            int v = 0, c = 0;
+            if (i < u1) {
+                const int2 e = g.adj[i];
+                v = e.x;
+                c = e.y;
+                const int lv = g.rp[v + 1] - g.rp[v];
+                cand = lv > lu || (lv == lu && v > u);
+                if (cand && lo <= 2) {
+                    const long long dv = g.deg[v];
+                    const bool pr12 = (lo <= 1 && level >= 1 && (long long)c >= lam) ||
+                                      (level >= 2 && 2LL * c > (du < dv ? du : dv));
+                    cand = !pr12;
+                }
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, cand);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int vv = __shfl_sync(0xffffffffu, v, l);
+                const long long cc = __shfl_sync(0xffffffffu, c, l);
+                const int v0 = g.rp[vv], lv = g.rp[vv + 1] - v0;
+                const long long dv = g.deg[vv];
+                long long pr4 = 0;
+                bool pr3 = false;
+                for (int k = u0 + lane; k < u1; k += 32) {
+                    const int2 x = g.adj[k];  // w = x.x, c(u, w) = x.y
+                    if (x.x == vv) continue;
+                    const int cvw = find_in_global(g.adj + v0, lv, x.x);
+                    if (cvw == 0) continue;
+                    const long long cuw = x.y;
+                    if (2 * (cc + cuw) > du && 2 * (cc + cvw) > dv) pr3 = true;
+                    pr4 += cuw < cvw ? cuw : cvw;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) pr4 += __shfl_xor_sync(0xffffffffu, pr4, o);
+                const bool ok = __any_sync(0xffffffffu, pr3) || (level >= 4 && cc + pr4 >= lam);
+                if (ok && lane == 0 && uf_union(par, u, vv)) ++local;
+            }
+        }
+    }
+    if (local) atomicAdd(unions, (unsigned long long)local);
+}
+
 int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int budget,
                     cudaStream_t s) {
     if (level <= 0 || lo > level || g.arcs == 0) return MC_OK;
     int blocks = (int)(((g.arcs > g.n ? g.arcs : g.n) + 255) / 256);
     int cap = num_sms() * 16;
     if (blocks > cap) blocks = cap;
-    ++::mc::g_launches; k_pr<<<blocks, 256, 0, s>>>(g, w.par, lam, lo, level, budget,
-                                reinterpret_cast<unsigned long long *>(&w.st->unions));
+    unsigned long long *un = reinterpret_cast<unsigned long long *>(&w.st->unions);
+    if (lo <= 2) { ++::mc::g_launches; k_pr<<<blocks, 256, 0, s>>>(g, w.par, lam, lo, level, un); }
+    if (level >= 3) {
+        long long wb = ((long long)g.n + kPrWarps - 1) / kPrWarps;
+        const long long cap = (long long)num_sms() * 8;
+        if (wb > cap) wb = cap;
+        ++::mc::g_launches; k_pr34<<<(int)wb, kPrWarps * 32, 0, s>>>(g, w.par, lam, lo, level, budget, un);
+    }
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }

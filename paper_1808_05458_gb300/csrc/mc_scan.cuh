@@ -514,7 +514,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             int kn = 0, ko = -1;
             if (s2 >= 0) {
                 int r_old = rv[s2];
-                if (PRECHECK && r_old == 0 && *(volatile int *)&A.T[y] != 0) {
+                if (PRECHECK && r_old == 0 && *(volatile int *)&A.T[y] > 0) {
                     rv[s2] = kDone;  // owned by another scan: blacklisted
                     cnt.black++;
                     r_old = kDone;
