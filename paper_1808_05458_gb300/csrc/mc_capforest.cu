@@ -89,6 +89,12 @@ __device__ void scan_driver(const ScanArgs &A, Counters &cnt, ScanFn scan) {
     }
 }
 
+// Blacklisting at first touch (PRECHECK in scan_one) is off: a vertex another
+// scan owns still collects r-value (and can be united by its threshold
+// crossing, as in Alg. 1, which blacklists at the pop); measured on RHG 2^20
+// and 2^21 the extra unions outweigh the longer scans
+constexpr bool kPrecheck = false;
+
 // concurrent scans with the list bucket queue (any cap)
 template <int WPB, int HC, int NB>
 __global__ void __launch_bounds__(WPB * 32)
@@ -115,7 +121,7 @@ k_capforest(ScanArgs A, int fifo) {
         __syncwarp();
         q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
         q.coarse = q.C + 1 > NB;
-        scan_one<HashTable<HC, ScanSmem<HC, NB>>, SmemQ<HC, NB>, true>(A, tab, q, start, sid, cnt);
+        scan_one<HashTable<HC, ScanSmem<HC, NB>>, SmemQ<HC, NB>, kPrecheck>(A, tab, q, start, sid, cnt);
     });
 }
 
@@ -139,7 +145,7 @@ k_capforest_bit(ScanArgs A) {
         if (lane == 0) sm.used = 0;
         __syncwarp();
         q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
-        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, true>(A, tab, q, start, sid, cnt);
+        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, kPrecheck>(A, tab, q, start, sid, cnt);
     });
 }
 

@@ -449,7 +449,11 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         q_update(q, lane == 0, s, -1, 0);
     }
     long long alpha = 0, best = LLONG_MAX;
-    long long L_solo = SOLO ? ld_volatile_i64(&A.st->lam) : 0;
+    // lambda-hat as of the scan's start, lowered by the scan's own alpha: a
+    // bound other scans lowered meanwhile is picked up at the next scan (a
+    // larger bound is still the weight of a cut, so every union stays valid,
+    // and one L2 read per pop is saved)
+    long long L_solo = ld_volatile_i64(&A.st->lam);
     int nS = 0, best_len = 0;
     bool alpha_ok = true, stop = false;
     cnt.scans++;
@@ -476,7 +480,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         int a0 = 0, a1 = 0;
         if (lane == 0) {
             A.order[x] = nS;
-            L = SOLO ? L_solo : ld_volatile_i64(&A.st->lam);
+            L = L_solo;
             a0 = A.g.rp[x];
             a1 = A.g.rp[x + 1];
             dx = A.g.deg[x];
