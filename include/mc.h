@@ -70,7 +70,8 @@ typedef struct mc_options {
                                 scans unite < n/4 vertices; default 4           */
     int32_t scans_per_round; /* concurrent CAPFOREST warps, 0 = auto           */
     int32_t region_budget;   /* max vertices touched by one scan, 0 = auto
-                                (192; 320 on graphs with >= 48 arcs/vertex)  */
+                                (192; 320 on graphs with >= 48 arcs/vertex;
+                                64 on graphs below 2^17 vertices)            */
     int32_t lp_iters;        /* label-propagation sweeps for MC_BOUND_LP, 0=auto*/
     uint64_t seed;           /* start vertices / LP parity                      */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = the graph's own */

@@ -403,8 +403,10 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
     // default region budget, measured on RHG: 192 touched vertices per scan
-    // (one 256-slot table), 320 on graphs averaging >= 48 arcs per vertex
-    int budget = cfg.budget > 0 ? cfg.budget : (g.arcs >= 48LL * g.n ? 320 : 192);
+    // (one 256-slot table), 320 on graphs averaging >= 48 arcs per vertex;
+    // 64 below 2^17 vertices, where the launch lasts as long as its longest
+    // scan rather than its total work
+    int budget = cfg.budget > 0 ? cfg.budget : (g.n < 131072 ? 64 : (g.arcs >= 48LL * g.n ? 320 : 192));
     constexpr int WPB = 4;
     int rc;
     if (cfg.lam_hint > 0 && cfg.lam_hint < 64 && !cfg.pq_fifo && budget <= 768) {

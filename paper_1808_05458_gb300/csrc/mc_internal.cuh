@@ -275,6 +275,17 @@ __device__ __forceinline__ int uf_find(int *par, int x) {
     }
 }
 
+// as uf_union; *root = the root of the merged set (its smallest member)
+__device__ __forceinline__ bool uf_union_root(int *par, int a, int b, int *root) {
+    while (true) {
+        a = uf_find(par, a);
+        b = uf_find(par, b);
+        if (a == b) { *root = a; return false; }
+        if (a > b) { int t = a; a = b; b = t; }
+        if (atomicCAS(&par[b], b, a) == b) { *root = a; return true; }
+    }
+}
+
 __device__ __forceinline__ bool uf_union(int *par, int a, int b) {
     while (true) {
         a = uf_find(par, a);

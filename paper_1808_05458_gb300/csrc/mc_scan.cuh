@@ -500,6 +500,9 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         }
         cnt.verts++;
         cnt.arcs += a1 - a0;
+        // unions of this pop all involve x: they start their find from the
+        // last root seen for x's set (any member of the set finds its root)
+        int xh = x;
         for (int i0 = a0; i0 < a1; i0 += 32) {
             int i = i0 + lane;
             bool v = i < a1;
@@ -538,8 +541,11 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
                 const unsigned jm = __ballot_sync(0xffffffffu, join);
                 if (join) A.pairs[cnt.npairs + __popc(jm & ((1u << lane) - 1u))] = ((u64)(u32)x << 32) | (u32)y;
                 cnt.npairs += __popc(jm);
-            } else if (join && uf_union(A.par, x, y)) {
-                cnt.unions++;
+            } else {
+                int rt = INT_MAX;
+                if (join && uf_union_root(A.par, xh, y, &rt)) cnt.unions++;
+                rt = __reduce_min_sync(0xffffffffu, rt);
+                if (rt != INT_MAX) xh = rt;
             }
             // a full pool is rebuilt from the live slots (they already hold
             // this chunk's new keys); a table that cannot rebuild ends the scan
