@@ -16,6 +16,7 @@
 // clamp), compacted into the next CSR.
 // Warps take graphs from a shared queue ordered by size (largest first).
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -565,6 +566,12 @@ struct BatchCtx {
     void *io = nullptr;
     size_t io_bytes = 0;
     cudaStream_t stream = nullptr;
+    // the captured {reset the work counter, persistent launch} of the last
+    // batch layout; replayed while the layout (and so every kernel
+    // argument) is unchanged
+    cudaGraphExec_t exec = nullptr;
+    unsigned char key[sizeof(BatchIn) + 3 * sizeof(int)] = {};
+    long long replays = 0;
 };
 std::mutex g_batch_mutex;
 BatchCtx g_batch[64];
@@ -682,7 +689,7 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
     }
     MC_CUDA(cudaMemcpyAsync(io + o_ord, order.data(), 4 * (size_t)G, cudaMemcpyHostToDevice, s));
     if (bitmaps) MC_CUDA(cudaMemcpyAsync(io + o_boff, bitmap_word_off, 8 * (G + 1), cudaMemcpyHostToDevice, s));
-    MC_CUDA(cudaMemsetAsync(io + o_next, 0, 4, s));
+
 
     BatchIn B;
     B.G = G;
@@ -706,8 +713,41 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
     cudaEvent_t ea, eb;
     cudaEventCreate(&ea);
     cudaEventCreate(&eb);
+    // one persistent launch under a captured CUDA graph (re-captured when
+    // the batch layout changes)
+    int rc = MC_OK;
+    {
+        unsigned char key[sizeof(ctx.key)];
+        memcpy(key, &B, sizeof(BatchIn));
+        const int extra[3] = {shape, warps, (int)(o.cuda_stream != nullptr)};
+        memcpy(key + sizeof(BatchIn), extra, sizeof(extra));
+        if (!ctx.exec || memcmp(key, ctx.key, sizeof(key)) != 0) {
+            if (ctx.exec) { cudaGraphExecDestroy(ctx.exec); ctx.exec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            MC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaMemsetAsync(io + o_next, 0, 4, s);
+            if (ce == cudaSuccess) rc = run_batch(shape, B, warps, s);
+            cudaError_t ee = cudaStreamEndCapture(s, &graph);
+            if (ce != cudaSuccess || ee != cudaSuccess || rc != MC_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                if (rc != MC_OK) return rc;
+                set_cuda_error(ce != cudaSuccess ? ce : ee, "batch graph capture");
+                return MC_ECUDA;
+            }
+            cudaError_t ie = cudaGraphInstantiate(&ctx.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                ctx.exec = nullptr;
+                set_cuda_error(ie, "cudaGraphInstantiate(batch)");
+                return MC_ECUDA;
+            }
+            memcpy(ctx.key, key, sizeof(key));
+        } else {
+            ++ctx.replays;
+        }
+    }
     cudaEventRecord(ea, s);
-    int rc = run_batch(shape, B, warps, s);
+    MC_CUDA(cudaGraphLaunch(ctx.exec, s));
     cudaEventRecord(eb, s);
     if (rc != MC_OK) {
         cudaEventDestroy(ea);

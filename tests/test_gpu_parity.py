@@ -364,6 +364,18 @@ def test_batch_small(mc):
     _check_batch_sides(b, lam, bits, boff, range(48))
 
 
+def test_batch_graph_replay(mc):
+    # the persistent launch is captured once per batch layout and replayed:
+    # repeated calls, then another layout, then the first again
+    b1, b2 = graphgen.batch(11, G=64), graphgen.batch(12, G=40)
+    ref1 = [oracle.noi(*graphgen.batch_graph(b1, k))[0] for k in range(64)]
+    ref2 = [oracle.noi(*graphgen.batch_graph(b2, k))[0] for k in range(40)]
+    for b, ref in [(b1, ref1), (b1, ref1), (b1, ref1), (b2, ref2), (b1, ref1)]:
+        lam, bits, boff, _ = mc.batch_min_cut(*b, bitmaps=True)
+        assert list(lam) == ref
+        _check_batch_sides(b, lam, bits, boff, range(len(ref)))
+
+
 def _concat(graphs):
     rps, cols, ws, voff, aoff = [], [], [], [0], [0]
     for rp, col, w in graphs:
