@@ -463,9 +463,16 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         int x = tab.vertex(s);
         int rx = rv[s];
         __syncwarp();
+        // the row offsets and degree go out with the claim (wasted on a
+        // blacklisted pop, but one round trip instead of two otherwise)
         int old = 0;
+        long long L = 0, dx = 0;
+        int a0 = 0, a1 = 0;
         if (lane == 0) {
             rv[s] = kDone;
+            a0 = A.g.rp[x];
+            a1 = A.g.rp[x + 1];
+            dx = A.g.deg[x];
             if (SOLO) A.T[x] = sid;
             else old = atomicCAS(&A.T[x], 0, sid);
         }
@@ -476,14 +483,9 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
                 continue;
             }
         }
-        long long L = 0, dx = 0;
-        int a0 = 0, a1 = 0;
         if (lane == 0) {
             A.order[x] = nS;
             L = L_solo;
-            a0 = A.g.rp[x];
-            a1 = A.g.rp[x + 1];
-            dx = A.g.deg[x];
         }
         L = __shfl_sync(0xffffffffu, L, 0);
         dx = __shfl_sync(0xffffffffu, dx, 0);
