@@ -125,8 +125,8 @@ int mc_options_default(mc_options *opt);
  *            (they are copied) and must call mc_graph_destroy().
  * Errors: MC_EINVAL for n < 2, a bad row_ptr, a neighbour out of range, a
  * negative weight, or (unless trusted) an arc (u,v,c) without its mirror
- * (v,u,c) after merging parallel arcs; MC_EOVERFLOW if a weighted degree
- * reaches 2^62; MC_ENOMEM; MC_ECUDA.
+ * (v,u,c) after merging parallel arcs; MC_EOVERFLOW if parallel arcs sum
+ * past INT32_MAX or a weighted degree reaches 2^62; MC_ENOMEM; MC_ECUDA.
  */
 int mc_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col,
                     const int32_t *w, int32_t flags, mc_graph **out);
@@ -148,7 +148,7 @@ int mc_graph_size(const mc_graph *g, int64_t *n, int64_t *m);
  * A disconnected graph has lambda = 0 and the side is every component but
  * vertex 0's.  The call is synchronous: it returns after the device work.
  * Errors: MC_EINVAL (NULL g/lambda_out), MC_EOVERFLOW (minimum weighted
- * degree >= 2^31 - 1, which the int32 scan arithmetic cannot hold),
+ * degree >= 2^31 - 3, which the int32 scan arithmetic cannot hold),
  * MC_ECUDA, MC_ETIMEOUT, MC_EINTERNAL.
  */
 int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,

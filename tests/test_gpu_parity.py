@@ -238,6 +238,50 @@ def test_disconnected_components_side(mc, opts):
     assert res.lam == 0 and side.sum() == 1 and side[-1] == 1
 
 
+@pytest.mark.parametrize("hub_w", [1, 2, 7])
+def test_hub_rows_passed_over(mc, hub_w):
+    # a wheel whose hub row (6000 arcs) is longer than the concurrent scans
+    # take: the hub is never scanned by them, only touched and united
+    k = 6000
+    rim = np.arange(k)
+    src = np.concatenate([rim, rim])
+    dst = np.concatenate([(rim + 1) % k, np.full(k, k)])
+    wt = np.concatenate([np.full(k, 3), np.full(k, hub_w)])
+    g = graphgen.from_edges(k + 1, src, dst, wt)
+    ref = oracle.noi(*g)[0]
+    assert ref == min(6 + hub_w, 2 * 3 + 2 * hub_w, k * hub_w)
+    for tail in (0, -1):
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(tail_vertices=tail))
+        check_cut(mc, g, res, ref)
+
+
+def test_weight_limits(mc):
+    big = 2**31 - 4
+    # the largest minimum degree the int32 scans accept (2^31 - 3 and up are
+    # refused)
+    g = graphgen.from_edges(3, np.array([0, 1]), np.array([1, 2]), np.array([big, big]))
+    with mc.Graph(*g) as G:
+        res = G.min_cut()
+    check_cut(mc, g, res, big)
+    g = graphgen.from_edges(3, np.array([0, 1]), np.array([1, 2]), np.array([big + 1, big + 1]))
+    with mc.Graph(*g) as G:
+        with pytest.raises(mc.MinCutError) as e:
+            G.min_cut()
+    assert e.value.code == mc.MC_EOVERFLOW
+    # parallel arcs summing past INT32_MAX are refused when merged
+    g = graphgen.from_edges(2, np.array([0, 0, 0]), np.array([1, 1, 1]), np.array([2**30] * 3))
+    with pytest.raises(mc.MinCutError) as e:
+        mc.Graph(*g)
+    assert e.value.code == mc.MC_EOVERFLOW
+    # a minimum degree past the scans' int32 range
+    g = graphgen.complete(4, 2**30)
+    with mc.Graph(*g) as G:
+        with pytest.raises(mc.MinCutError) as e:
+            G.min_cut()
+    assert e.value.code == mc.MC_EOVERFLOW
+
+
 def test_tree_and_path(mc):
     for seed in range(5):
         g = graphgen.random_tree(3000, seed)
