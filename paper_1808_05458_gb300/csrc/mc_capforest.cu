@@ -298,9 +298,6 @@ __global__ void k_scan_reset(Status *st) {
     st->best_len = 0;
 }
 
-__global__ void k_fill_i32(int *a, int n, int v) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
-}
 
 template <int WPB, int HC, int NBK>
 static int launch_parallel_bit(const ScanArgs &A, int warps_wanted, cudaStream_t s) {

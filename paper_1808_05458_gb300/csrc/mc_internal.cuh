@@ -176,9 +176,6 @@ int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s)
 // minimum degree + smallest argmin into st->mindeg / st->argmin
 int min_degree(const DevGraph &g, Work &w, cudaStream_t s);
 
-// Padberg-Rinaldi tests 1..level against lam: unions into w.par
-int pr_tests(const DevGraph &g, Work &w, i64 lam, int level, cudaStream_t s);
-
 // concurrent capped CAPFOREST (Alg. 1): unions into w.par, alpha updates
 // into st->lam, owners in w.T / w.order, records in w.rec_*.
 struct ScanConfig {
