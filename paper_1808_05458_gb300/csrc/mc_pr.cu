@@ -157,8 +157,4 @@ int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int 
     return MC_OK;
 }
 
-int pr_tests(const DevGraph &g, Work &w, i64 lam, int level, cudaStream_t s) {
-    return pr_tests_budget(g, w, lam, 1, level, 64, s);
-}
-
 }  // namespace mc
