@@ -91,7 +91,10 @@ typedef struct mc_stats {
     int64_t n_input;         /* vertices of the canonical input                 */
     int64_t m_input;         /* undirected edges of the canonical input         */
     double ms_total;         /* device time of the whole call                   */
-    double ms_bound;         /* initial bound (degrees / LP)                    */
+    double ms_bound;         /* initial bound (degrees / LP / proposer); with
+                                the LP bound this includes the exact solve of
+                                the clustered remainder, whose phases are also
+                                counted below                                  */
     double ms_pr;            /* Padberg-Rinaldi tests                           */
     double ms_capforest;     /* CAPFOREST scans (parallel + fallback)           */
     double ms_contract;      /* union-find flatten, relabel, sort, rebuild      */

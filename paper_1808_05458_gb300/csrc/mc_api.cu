@@ -395,6 +395,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
 
     // the label-propagation bound (VieCut, Sec. 2.3 / 3.1.1) on a contracted
     // copy: every candidate is the weight of a real cut of G
+    Timer bound_timer(s);
     if (o.bound == MC_BOUND_LP || o.bound == MC_BOUND_BEST) {
         MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); }));
         MC_TRY(iota_i32(w.orig, n0, s));
@@ -413,7 +414,8 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         }
     }
     S.bound_initial = lam;
-    S.ms_bound = ph.ms();
+    S.ms_bound = bound_timer.ms();
+    ph.ms();  // restart the phase timer
     const int bound_rounds = rounds;
     rounds = 0;
     MC_TRY(exact_loop(g->G0, &g->Ga));
