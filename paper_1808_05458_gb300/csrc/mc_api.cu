@@ -26,6 +26,8 @@ struct mc_graph {
     Work w;
     i64 delta0 = 0;
     int argmin0 = 0;
+    i64 wmax0 = 0;          // largest arc weight of G0
+    i64 two_arc_rows0 = 0;  // rows of G0 with exactly two arcs
     bool device_ptrs = false;
 };
 
@@ -131,10 +133,13 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
     }
     rc = canonicalize(n, drp, dcol, dw, (flags & MC_TRUST_INPUT) == 0, g->G0, g->w, s);
     if (rc == MC_OK) rc = min_degree(g->G0, g->w, s);
+    if (rc == MC_OK) rc = graph_stats(g->G0, g->w, s);
     if (rc == MC_OK) rc = status_read(g->w, s);
     if (rc == MC_OK) {
         g->delta0 = g->w.h_st->mindeg;
         g->argmin0 = g->w.h_st->argmin;
+        g->wmax0 = g->w.h_st->count;
+        g->two_arc_rows0 = g->w.h_st->count2;
         if (g->delta0 >= (1LL << 62)) rc = MC_EOVERFLOW;
     }
     if (rc != MC_OK) {
@@ -288,7 +293,12 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         cfg.round = rounds + guard;
         MC_TRY(union_find_init(w.par, cur.n, s));
         MC_TRY(round_reset(w, lam, s));
-        if (o.pr_level > 0) {
+        // PR1/PR2 and the degree-2 rule on the input graph pass nothing when
+        // every weight is below lambda-hat and half of delta and no row has
+        // two arcs (unit-weight graphs with delta >= 3): skipped there
+        const bool pr12_idle = cur.rp == g->G0.rp && g->wmax0 < lam && 2 * g->wmax0 <= g->delta0 &&
+                               g->two_arc_rows0 == 0;
+        if (o.pr_level > 0 && !pr12_idle) {
             MC_TRY(pr_tests_budget(cur, w, lam, 1, o.pr_level < 2 ? o.pr_level : 2, 64, s));
             bytes += cur.arcs * 16;
         }

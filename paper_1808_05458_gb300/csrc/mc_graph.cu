@@ -390,6 +390,34 @@ __global__ void k_zero_count(Status *st) {
     st->count2 = 0;
 }
 
+// largest arc weight (st->count) and number of rows with exactly two arcs
+// (st->count2): when max weight < lambda-hat, 2 * max weight <= delta and no
+// row has two arcs, PR1, PR2 and the degree-2 rule cannot unite anything
+__global__ void k_graph_stats(const DevGraph g, Status *st) {
+    int wmax = 0;
+    long long two = 0;
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < g.arcs; j += (i64)gridDim.x * blockDim.x)
+        wmax = max(wmax, g.adj[j].y);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += gridDim.x * blockDim.x)
+        two += g.rp[v + 1] - g.rp[v] == 2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        two += __shfl_xor_sync(0xffffffffu, two, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (wmax) atomicMax(reinterpret_cast<unsigned long long *>(&st->count), (unsigned long long)wmax);
+        if (two) atomicAdd(reinterpret_cast<unsigned long long *>(&st->count2), (unsigned long long)two);
+    }
+}
+
+int graph_stats(const DevGraph &g, Work &w, cudaStream_t s) {
+    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    ++::mc::g_launches; k_graph_stats<<<grid_for(g.arcs > g.n ? g.arcs : g.n), kThreads, 0, s>>>(g, w.st);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 static int bits_for(u64 x) {
     int b = 0;
     while (x) { ++b; x >>= 1; }

@@ -175,6 +175,8 @@ int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s)
 
 // minimum degree + smallest argmin into st->mindeg / st->argmin
 int min_degree(const DevGraph &g, Work &w, cudaStream_t s);
+// largest arc weight into st->count, rows with exactly two arcs into st->count2
+int graph_stats(const DevGraph &g, Work &w, cudaStream_t s);
 
 // concurrent capped CAPFOREST (Alg. 1): unions into w.par, alpha updates
 // into st->lam, owners in w.T / w.order, records in w.rec_*.
