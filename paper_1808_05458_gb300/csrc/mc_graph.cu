@@ -757,9 +757,11 @@ int round_reset(Work &w, i64 lam, cudaStream_t s) {
 }
 
 // canonical polarity: vertex 0 on side 0; clear the bits past n0
-__global__ void k_side_canon(u32 *bits, int n0) {
+__global__ void k_side_flip(const u32 *bits, int *flip) { *flip = (int)(bits[0] & 1u); }
+
+__global__ void k_side_canon(u32 *bits, int n0, const int *flip_p) {
     const int nw = (n0 + 31) / 32;
-    const bool flip = bits[0] & 1u;
+    const bool flip = *flip_p != 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
         u32 v = flip ? ~bits[i] : bits[i];
         if (i == nw - 1 && (n0 & 31)) v &= (1u << (n0 & 31)) - 1u;
@@ -768,8 +770,9 @@ __global__ void k_side_canon(u32 *bits, int n0) {
 }
 
 int side_canon(Work &w, int n0, cudaStream_t s) {
-    // one block: bits[0] is read by every thread before any write
-    ++::mc::g_launches; k_side_canon<<<1, 1024, 0, s>>>(w.best_side, n0);
+    // vertex 0's bit is read by its own launch before any word is rewritten
+    ++::mc::g_launches; k_side_flip<<<1, 1, 0, s>>>(w.best_side, &w.st->flip);
+    ++::mc::g_launches; k_side_canon<<<side_grid(n0), kThreads, 0, s>>>(w.best_side, n0, &w.st->flip);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }

@@ -88,7 +88,7 @@ struct Status {
     int scan_ids;       // scan id counter
     int best_scan;      // scan whose alpha set lambda-hat (or -1)
     int best_len;       // prefix length of that scan
-    int pad;
+    int flip;           // the side bitmap's vertex-0 bit, before canonical polarity
 };
 
 constexpr int kErrAsym = 1;       // asymmetric input
