@@ -200,6 +200,15 @@ int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
 /* Message for an error code (thread-local detail for MC_ECUDA). */
 const char *mc_strerror(int code);
 
+/*
+ * mc_test_fail_alloc_after -- fault-injection hook for tests (no paper
+ * counterpart): the device allocation after the next `k` ones fails with
+ * MC_ENOMEM, as if the device were full; k < 0 switches the hook off.  The
+ * count is process-wide and one-shot (it switches itself off after firing).
+ * Returns MC_OK.
+ */
+int mc_test_fail_alloc_after(int64_t k);
+
 /* ---- learned bound proposer -----------------------------------------------
  * A 3-layer message-passing network (hidden 64, BF16 activations, FP32
  * sums, tensor-core dense transforms) scores every vertex; the best sweep

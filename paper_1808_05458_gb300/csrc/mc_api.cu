@@ -653,6 +653,11 @@ int mc_proposer_bound(mc_proposer *p, mc_graph *g, int64_t *cut, uint32_t *side)
     return MC_OK;
 }
 
+int mc_test_fail_alloc_after(int64_t k) {
+    test_fail_alloc_after(k);
+    return MC_OK;
+}
+
 const char *mc_strerror(int code) {
     static thread_local std::string msg;
     switch (code) {

@@ -3,6 +3,7 @@
 // The radix sort and scan are the building blocks of the CSR rebuild by
 // "radix sort plus segmented sum" that replaces the paper's concurrent hash
 // table in parallel graph contraction (Sec. 3.2).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -38,7 +39,21 @@ static void retain_pool_memory() {
     done[dev] = true;
 }
 
+// fault-injection hook (mc_test_fail_alloc_after): allocations to pass
+// before one fails; -1 = off
+static std::atomic<long long> g_fail_alloc_after{-1};
+
+void test_fail_alloc_after(long long k) { g_fail_alloc_after.store(k < 0 ? -1 : k); }
+
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    long long k = g_fail_alloc_after.load();
+    while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) {
+        *p = nullptr;
+        set_error_detail("injected allocation failure");
+        return MC_ENOMEM;
+    }
     retain_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {

@@ -72,7 +72,7 @@ EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_grap
            "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc",
            "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
            "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
-           "mc_proposer_bound")
+           "mc_proposer_bound", "mc_test_fail_alloc_after")
 
 
 def library_path() -> str:
@@ -97,6 +97,7 @@ def load_library():
     lib.mc_graph_size.argtypes = [vp, P(i64), P(i64)]
     lib.mc_min_cut.argtypes = [vp, P(McOptions), P(i64), vp, P(McStats)]
     lib.mc_batch_min_cut.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), vp, vp, vp, P(McStats)]
+    lib.mc_test_fail_alloc_after.argtypes = [i64]
     lib.mc_strerror.argtypes = [ctypes.c_int]
     lib.mc_strerror.restype = ctypes.c_char_p
     lib.mc_graph_export.argtypes = [vp, vp, vp, vp]
@@ -149,6 +150,12 @@ def options(**kw) -> McOptions:
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
     return o
+
+
+def test_fail_alloc_after(k: int):
+    """Fault-injection hook: the device allocation after the next k fails
+    with MC_ENOMEM (k < 0: off)."""
+    load_library().mc_test_fail_alloc_after(k)
 
 
 def bitmap_to_side(bits: np.ndarray, n: int) -> np.ndarray:

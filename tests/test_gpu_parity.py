@@ -591,3 +591,32 @@ def test_lp_bound_lambda_unchanged(mc):
         with mc.Graph(*g) as G:
             res = G.min_cut(mc.options(bound=mc.MC_BOUND_LP, lp_iters=3))
         check_cut(mc, g, res, ref)
+
+
+def test_injected_allocation_failures(mc):
+    # host-side fault injection: every device allocation of graph creation,
+    # solve and batch in turn fails; each call reports MC_ENOMEM, leaves
+    # nothing behind, and the next call works
+    g = graphgen.random_connected(300, 900, seed=5, wmax=5)
+    ref = oracle.stoer_wagner(*g)[0]
+    b = graphgen.batch(3, G=16)
+    bref = [oracle.noi(*graphgen.batch_graph(b, k))[0] for k in range(16)]
+    failures = 0
+    try:
+        for k in range(64):
+            mc.test_fail_alloc_after(k)
+            try:
+                with mc.Graph(*g) as G:
+                    res = G.min_cut(mc.options(bound=1))
+                    assert res.lam == ref
+                lam = mc.batch_min_cut(*b)[0]
+                assert list(lam) == bref
+            except mc.MinCutError as e:
+                assert e.code == mc.MC_ENOMEM
+                failures += 1
+            mc.test_fail_alloc_after(-1)
+            with mc.Graph(*g) as G:
+                assert G.min_cut().lam == ref
+    finally:
+        mc.test_fail_alloc_after(-1)
+    assert failures > 10
