@@ -115,7 +115,7 @@ __global__ void k_relabel(const int *__restrict__ root, int *lab, int n) {
 // keeps its survivors in registers, ranks them with one block scan and
 // reserves their output range with a single atomic per chunk (a per-warp
 // atomic on one global counter serialises millions of times).
-constexpr int kEmitItems = 8;
+constexpr int kEmitItems = 4;
 constexpr int kEmitChunk = kEmitItems * kThreads;
 
 __device__ __forceinline__ int block_excl_scan_256(int v, int *total) {
