@@ -29,6 +29,7 @@ struct mc_graph {
     i64 wmax0 = 0;          // largest arc weight of G0
     i64 two_arc_rows0 = 0;  // rows of G0 with exactly two arcs
     bool device_ptrs = false;
+    std::vector<cudaEvent_t> events;  // phase-clock events, reused across calls
 };
 
 namespace {
@@ -55,6 +56,65 @@ struct Timer {
     }
 };
 
+// Phase times from events recorded at phase boundaries and read only once the
+// call has synchronised at its end, so the timing adds no waits: each mark
+// closes the interval since the previous mark and adds it to an accumulator
+// (or drops it); spans add the time between two marks of their own.
+struct PhaseClock {
+    std::vector<cudaEvent_t> &pool;
+    cudaStream_t s;
+    std::vector<double *> dst;                       // accumulator per interval
+    std::vector<std::pair<size_t, size_t>> span_ev;  // (begin, end) event indices
+    std::vector<double *> span_dst;
+    size_t used = 0;
+    PhaseClock(std::vector<cudaEvent_t> &p, cudaStream_t s_) : pool(p), s(s_) { mark(nullptr); }
+    size_t record() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        cudaEventRecord(pool[used], s);
+        return used++;
+    }
+    void mark(double *acc) {
+        record();
+        dst.push_back(acc);
+    }
+    size_t span_begin() {
+        const size_t i = record();
+        dst.push_back(nullptr);
+        return i;
+    }
+    void span_end(size_t b, double *acc) {
+        const size_t e = record();
+        dst.push_back(nullptr);
+        span_ev.emplace_back(b, e);
+        span_dst.push_back(acc);
+    }
+    // the last interval now (synchronises; for verbose output only)
+    double last_ms() {
+        float t = 0;
+        cudaEventSynchronize(pool[used - 1]);
+        cudaEventElapsedTime(&t, pool[used - 2], pool[used - 1]);
+        return t;
+    }
+    void finish() {
+        if (used) cudaEventSynchronize(pool[used - 1]);
+        for (size_t i = 1; i < used; ++i)
+            if (dst[i]) {
+                float t = 0;
+                cudaEventElapsedTime(&t, pool[i - 1], pool[i]);
+                *dst[i] += t;
+            }
+        for (size_t k = 0; k < span_ev.size(); ++k) {
+            float t = 0;
+            cudaEventElapsedTime(&t, pool[span_ev[k].first], pool[span_ev[k].second]);
+            *span_dst[k] += t;
+        }
+    }
+};
+
 int read_i32(const int *p, bool dev, int *out, cudaStream_t s) {
     if (!dev) {
         *out = *p;
@@ -69,6 +129,7 @@ void destroy_all(mc_graph *g) {
     if (!g) return;
     cudaStream_t s = g->stream;
     if (s) cudaStreamSynchronize(s);
+    for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     graph_free(g->G0, s);
     graph_free(g->Ga, s);
     graph_free(g->Gb, s);
@@ -223,7 +284,8 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     memset(&S, 0, sizeof(S));
     S.n_input = n0;
     S.m_input = g->arcs0 / 2;
-    Timer total(s), ph(s);
+    Timer total(s);
+    PhaseClock ph(g->events, s);
     i64 bytes = 0;
     const long long launches0 = g_launches;
     cudaEvent_t ka, kb;
@@ -281,12 +343,11 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             long long lt = lam;
             MC_TRY(tail_solve(cur, w, tail_n, &lt, o.seed ^ (u64)rounds, o.pr_level,
                               o.pq_order == MC_PQ_FIFO, n0, s));
-            const double t = ph.ms();
+            ph.mark(&S.ms_tail);
             if (verbose)
                 fprintf(stderr, "[mc] tail n=%d arcs=%lld lam %lld -> %lld (%.3f ms)\n", cur.n,
-                        (long long)cur.arcs, (long long)lam, lt, t);
+                        (long long)cur.arcs, (long long)lam, lt, ph.last_ms());
             lam = lt;
-            S.ms_tail += t;
             ++S.tail_launches;
             break;
         }
@@ -302,7 +363,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             MC_TRY(pr_tests_budget(cur, w, lam, 1, o.pr_level < 2 ? o.pr_level : 2, 64, s));
             bytes += cur.arcs * 16;
         }
-        S.ms_pr += ph.ms();
+        ph.mark(&S.ms_pr);
         // concurrent capped scans; returns the round's cumulative unions and
         // records a side if some scan's alpha lowered lambda-hat
         auto scan_round = [&](int budget, i64 *unions_out) -> int {
@@ -336,19 +397,19 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         };
         i64 unions = 0;
         MC_TRY(scan_round(cfg.budget, &unions));
-        S.ms_capforest += ph.ms();
+        ph.mark(&S.ms_capforest);
         // a poor round: the triangle tests PR3/PR4 add their unions
         if (o.pr_level >= 3 && unions * 4 < cur.n) {
             MC_TRY(pr_tests_budget(cur, w, lam, 3, o.pr_level, 64, s));
             MC_TRY(status_read(w, s));
             unions = w.h_st->unions;
             bytes += cur.arcs * 16;
-            S.ms_pr += ph.ms();
+            ph.mark(&S.ms_pr);
         }
         // nothing united: wide scans first, then one full scan (Alg. 2)
         if (unions == 0) {
             MC_TRY(scan_round(1536, &unions));
-            S.ms_capforest += ph.ms();
+            ph.mark(&S.ms_capforest);
         }
         if (unions == 0) {
             const i64 lam_before = lam;
@@ -370,13 +431,13 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
                 fprintf(stderr, "[mc] round %d full scan: unions=%lld lam=%lld\n", rounds,
                         (long long)unions, (long long)lam);
             if (unions == 0) {
-                S.ms_capforest += ph.ms();
+                ph.mark(&S.ms_capforest);
                 if (lam < lam_before) continue;  // lambda-hat dropped inside the scan: rescan
                 set_error_detail("full CAPFOREST scan marked no edge");
                 return MC_EINTERNAL;
             }
         }
-        S.ms_capforest += ph.ms();
+        ph.mark(&S.ms_capforest);
         // contraction; the orig map and the new minimum degree ride on its
         // final status read
         MC_TRY(contract_graph(cur, *nxt, w, lam, true, 0, s, [&]() -> int {
@@ -389,13 +450,10 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             lam = w.h_st->mindeg;
             MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
         }
-        {
-            double t = ph.ms();
-            S.ms_contract += t;
-            if (verbose)
-                fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld emitted=%lld (%.3f ms) lam=%lld\n", nxt->n,
-                        (long long)nxt->arcs, (long long)w.last_emitted, t, (long long)lam);
-        }
+        ph.mark(&S.ms_contract);
+        if (verbose)
+            fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld emitted=%lld (%.3f ms) lam=%lld\n", nxt->n,
+                    (long long)nxt->arcs, (long long)w.last_emitted, ph.last_ms(), (long long)lam);
         cur = *nxt;
         nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
         ++rounds;
@@ -405,7 +463,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
 
     // the label-propagation bound (VieCut, Sec. 2.3 / 3.1.1) on a contracted
     // copy: every candidate is the weight of a real cut of G
-    Timer bound_timer(s);
+    const size_t bound_begin = ph.span_begin();
     if (o.bound == MC_BOUND_LP || o.bound == MC_BOUND_BEST) {
         MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); }));
         MC_TRY(iota_i32(w.orig, n0, s));
@@ -424,8 +482,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         }
     }
     S.bound_initial = lam;
-    S.ms_bound = bound_timer.ms();
-    ph.ms();  // restart the phase timer
+    ph.span_end(bound_begin, &S.ms_bound);
     const int bound_rounds = rounds;
     rounds = 0;
     MC_TRY(exact_loop(g->G0, &g->Ga));
@@ -441,6 +498,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     S.kernel_launches = g_launches - launches0;
     out.lam = lam;
     S.ms_total = total.ms();
+    ph.finish();
     return MC_OK;
 }
 
