@@ -242,8 +242,11 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the public API with host buffers: H2D of the CSR
     # from pinned host memory, canonicalise + solve on the device, D2H of
-    # lambda and the side bitmap
-    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in (rp, col, w)]
+    # lambda and the side bitmap.  An unweighted graph is passed as it is
+    # stored by a user, without a weight array (mc_graph_create with w NULL).
+    unweighted = bool((w == 1).all())
+    host = (rp, col) if unweighted else (rp, col, w)
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in host]
     e2e_steps = max(1, min(args.steps, 5))
     with mc.Graph(*pinned) as Ge:  # untimed: the allocator's first growth
         Ge.min_cut(mc.options(seed=args.seed))
@@ -255,7 +258,7 @@ def run_gpu(args, rank, world, local_rank):
         assert r2.lam == lam
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
-    h2d = rp.nbytes + col.nbytes + w.nbytes
+    h2d = sum(a.nbytes for a in host)
     d2h = 8 + 4 * ((n + 31) // 32)
 
     # dominant kernel: the concurrent CAPFOREST scan kernel
@@ -298,6 +301,8 @@ def run_gpu(args, rank, world, local_rank):
                    f"rhg_n2^{args.rhg_log2}_deg32_gamma5_lcc_unit", "n": n, "m": m, "lambda": lam,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; CSR 402 MB > L2",
+                   "e2e_input": "row_ptr + col, unweighted (w NULL)" if unweighted
+                                 else "row_ptr + col + w",
                    "rounds": s0["rounds"], "fallback_rounds": s0["fallback_rounds"],
                    "ms_phase": {k: s0[k] for k in ("ms_bound", "ms_pr", "ms_capforest",
                                                     "ms_contract")},

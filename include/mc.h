@@ -83,7 +83,10 @@ typedef struct mc_options {
     int32_t reserved_;       /* must be 0                                       */
 } mc_options;
 
-/* Per-call statistics (all optional). */
+/* Per-call statistics (all optional). The ms_* phase times come from CUDA events
+ * recorded on the call's stream at the phase boundaries and read once when the call
+ * ends (no synchronisation between phases); device idle time between two phases is
+ * counted in ms_total only. */
 typedef struct mc_stats {
     int32_t rounds;          /* contraction rounds of Alg. 2                    */
     int32_t fallback_rounds; /* rounds that needed the full CAPFOREST scan      */
@@ -120,7 +123,8 @@ int mc_options_default(mc_options *opt);
  *   n        vertices, >= 2 (a cut needs two non-empty sides, Sec. 2.1)
  *   row_ptr  n+1 int32 offsets, row_ptr[0] = 0, non-decreasing
  *   col      row_ptr[n] int32 neighbours in [0, n)
- *   w        row_ptr[n] int32 weights >= 0
+ *   w        row_ptr[n] int32 weights >= 0, or NULL for an unweighted graph
+ *            (every arc has weight 1; nothing is read or copied for it)
  *   flags    MC_DEVICE_PTRS: the arrays live on the device (read on the
  *            graph's stream); otherwise host memory.  MC_TRUST_INPUT: skip
  *            the symmetry check.

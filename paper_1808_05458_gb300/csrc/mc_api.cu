@@ -162,7 +162,7 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
     int arcs_raw = 0;
     int rc = read_i32(row_ptr + n, dev, &arcs_raw, s);
     if (rc == MC_OK && arcs_raw < 0) rc = MC_EINVAL;
-    if (rc == MC_OK && arcs_raw > 0 && (!col || !w)) rc = MC_EINVAL;
+    if (rc == MC_OK && arcs_raw > 0 && !col) rc = MC_EINVAL;
     if (rc != MC_OK) {
         destroy_all(g);
         return rc;
@@ -181,7 +181,7 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
                                         cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && arcs_raw > 0)
             e = cudaMemcpyAsync(g->Ga.src, col, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && arcs_raw > 0)
+        if (e == cudaSuccess && arcs_raw > 0 && w)
             e = cudaMemcpyAsync(g->Gb.src, w, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             set_cuda_error(e, "cudaMemcpyAsync(input)");
@@ -190,7 +190,7 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
         }
         drp = g->Ga.rp;
         dcol = g->Ga.src;
-        dw = g->Gb.src;
+        dw = w ? g->Gb.src : nullptr;
     }
     rc = canonicalize(n, drp, dcol, dw, (flags & MC_TRUST_INPUT) == 0, g->G0, g->w, s);
     if (rc == MC_OK) rc = min_degree(g->G0, g->w, s);

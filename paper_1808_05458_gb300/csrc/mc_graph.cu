@@ -215,7 +215,8 @@ k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs, cons
     }
 }
 
-// raw input arcs: validate and emit (u, v, c) for u != v, c > 0
+// raw input arcs: validate and emit (u, v, c) for u != v, c > 0 (w == nullptr:
+// every arc has weight 1)
 __global__ void __launch_bounds__(kThreads)
 k_emit_raw(const int *__restrict__ rp, const int *__restrict__ col, const int *__restrict__ w, int n,
            i64 arcs, u64 *__restrict__ keys, int *__restrict__ vals, u64 *counter, int *err) {
@@ -249,7 +250,7 @@ k_emit_raw(const int *__restrict__ rp, const int *__restrict__ col, const int *_
                     }
                     u = lo;
                 }
-                const int v = col[i], c = w[i];
+                const int v = col[i], c = w ? w[i] : 1;
                 if (v < 0 || v >= n) atomicOr(err, kErrRange);
                 else if (c < 0) atomicOr(err, kErrNegW);
                 else if (u != v && c > 0) {
@@ -527,7 +528,7 @@ __global__ void k_clear_err(Status *st) { st->err = 0; }
 // flagging whether the input was canonical already (rows strictly
 // increasing, no self-loop, weights > 0; if not, the sort path rebuilds the
 // graph) and whether it is invalid (range, negative weight).  One warp per
-// row.
+// row.  w == nullptr: an unweighted graph, every arc of weight 1.
 __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict__ col,
                               const int *__restrict__ w, int n, DevGraph out, int *err, int *noncanon) {
     const int lane = threadIdx.x & 31;
@@ -537,7 +538,7 @@ __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict_
         const int a0 = rp[u], a1 = rp[u + 1];
         long long d = 0;
         for (int i = a0 + lane; i < a1; i += 32) {
-            const int v = col[i], c = w[i];
+            const int v = col[i], c = w ? w[i] : 1;
             if (v < 0 || v >= n) atomicOr(err, kErrRange);
             else if (c < 0) atomicOr(err, kErrNegW);
             if (v == u || c <= 0 || (i > a0 && col[i - 1] >= v)) bad = true;

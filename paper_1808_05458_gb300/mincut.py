@@ -182,29 +182,33 @@ class Graph:
 
     ``row_ptr``, ``col``, ``w``: int32 symmetric CSR, either numpy arrays
     (host) or int32 CUDA torch tensors (device, copied on the graph's stream).
+    ``w=None``: an unweighted graph (every arc has weight 1; no weight array
+    is copied).
     """
 
-    def __init__(self, row_ptr, col, w, trust: bool = False):
+    def __init__(self, row_ptr, col, w=None, trust: bool = False):
         lib = load_library()
         self._h = ctypes.c_void_p()
         flags = MC_TRUST_INPUT if trust else 0
         self.device_ptrs = hasattr(row_ptr, "data_ptr")
         if self.device_ptrs:
             import torch
-            for t in (row_ptr, col, w):
+            for t in (row_ptr, col) + ((w,) if w is not None else ()):
                 assert t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
             n = row_ptr.numel() - 1
             flags |= MC_DEVICE_PTRS
             torch.cuda.current_stream().synchronize()
             rc = lib.mc_graph_create(n, ctypes.c_void_p(row_ptr.data_ptr()),
                                      ctypes.c_void_p(col.data_ptr()),
-                                     ctypes.c_void_p(w.data_ptr()), flags, ctypes.byref(self._h))
+                                     ctypes.c_void_p(w.data_ptr() if w is not None else None),
+                                     flags, ctypes.byref(self._h))
         else:
             rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
             c = np.ascontiguousarray(col, dtype=np.int32)
-            ww = np.ascontiguousarray(w, dtype=np.int32)
+            ww = np.ascontiguousarray(w, dtype=np.int32) if w is not None else None
             n = len(rp) - 1
-            rc = lib.mc_graph_create(n, _ptr(rp), _ptr(c), _ptr(ww), flags, ctypes.byref(self._h))
+            rc = lib.mc_graph_create(n, _ptr(rp), _ptr(c), _ptr(ww) if ww is not None else None,
+                                     flags, ctypes.byref(self._h))
         _check(rc, "mc_graph_create")
         self.n = n
         nn, mm = ctypes.c_int64(), ctypes.c_int64()

@@ -360,6 +360,41 @@ def test_device_pointer_graph(mc):
     assert oracle.cut_weight(*g, side) == ref
 
 
+def test_unweighted_input(mc):
+    # w = NULL: every arc has weight 1, on both the one-pass build (canonical
+    # rows) and the sort path (parallel arcs become weight 2, self-loops drop)
+    import torch
+    rng = np.random.default_rng(7)
+    for i in range(24):
+        n = int(rng.integers(2, 40))
+        m = int(rng.integers(1, 4 * n))
+        u, v = rng.integers(0, n, size=m), rng.integers(0, n, size=m)
+        if i % 2 == 0:  # canonical: distinct edges, no self-loops
+            e = np.unique(np.stack([np.minimum(u, v), np.maximum(u, v)], 1)[u != v], axis=0)
+            u, v = e[:, 0], e[:, 1]
+        # odd i: the raw edge list with its parallel edges and self-loops
+        g = graphgen.from_edges(n, u, v)
+        ones = (g[0], g[1], np.ones_like(g[2]))
+        orp, ocol, ow = oracle.contract(*ones, np.arange(n, dtype=np.int32), n)
+        ref = oracle.brute_force(*ones)[0] if n <= 16 else oracle.noi(*ones)[0]
+        for dev in (False, True):
+            args = [torch.from_numpy(a.copy()).cuda() for a in ones[:2]] if dev else list(ones[:2])
+            with mc.Graph(*args) as G:
+                rp, col, w = G.export()
+                assert (rp == orp).all() and (col == ocol).all() and (w == ow).all()
+                res = G.min_cut()
+            assert res.lam == ref
+            assert oracle.cut_weight(*ones, res.side(n)) == ref
+    g = graphgen.rhg(3, 1 << 14, 16.0)
+    assert (g[2] == 1).all()
+    with mc.Graph(g[0], g[1]) as G:
+        assert G.min_cut().lam == oracle.noi(*g)[0]
+    # the symmetry check still applies
+    bad = (np.array([0, 1, 1], dtype=np.int32), np.array([1], dtype=np.int32))
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(*bad)
+
+
 def test_input_conventions(mc):
     # parallel arcs summed, self-loops and zero weights dropped
     g = graphgen.from_edges(4, np.array([0, 0, 1, 2, 3, 1, 2]), np.array([1, 1, 2, 3, 3, 3, 0]),
