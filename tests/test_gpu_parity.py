@@ -157,6 +157,30 @@ def test_capforest_round_medium_safe(mc):
         assert min(lam_out, lam_c) == lam_g
 
 
+@pytest.mark.parametrize("seed,logn,deg,unites", [(2, 14, 16.0, True), (5, 16, 32.0, True),
+                                                  (3, 13, 64.0, True), (6, 12, 90.0, False)])
+def test_capforest_round_rhg_safe(mc, seed, logn, deg, unites):
+    # thousands of concurrent scans on one graph, lambda-hat 3, 8, 29 and 42
+    # (each bitmap queue size): the round keeps min(lambda-hat, lambda(G/U))
+    # = lambda(G); at lambda-hat 42 (average degree 90) scans of 48-64
+    # vertices reach no threshold, which leaves the work to the full scan
+    g = graphgen.rhg(seed, 1 << logn, deg)
+    lam_g = oracle.noi(*g)[0]
+    d = oracle.degrees(*g)
+    for budget in (0, 48):
+        with mc.Graph(*g) as G:
+            lab, lam_out, unions = G.capforest_round(int(d.min()), mc.options(region_budget=budget, seed=seed))
+        assert_root_labels(lab)
+        assert lam_out >= lam_g and (unions > 0 or not unites)
+        roots, lab2 = np.unique(lab, return_inverse=True)
+        if len(roots) == 1:
+            assert lam_out == lam_g
+            continue
+        crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+        lam_c = oracle.noi(crp.astype(np.int32), ccol, cw.astype(np.int32))[0] if len(roots) >= 2 else lam_out
+        assert min(lam_out, lam_c) == lam_g
+
+
 # ------------------------------------------------------------ full solves --
 def test_random_tiny_min_cut(mc):
     rng = np.random.default_rng(4)
@@ -391,6 +415,39 @@ def test_unweighted_input(mc):
         assert G.min_cut().lam == oracle.noi(*g)[0]
     # the symmetry check still applies
     bad = (np.array([0, 1, 1], dtype=np.int32), np.array([1], dtype=np.int32))
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(*bad)
+
+
+def test_pinned_host_input(mc):
+    # page-locked host arrays (the end-to-end benchmark's inputs): the
+    # canonical graph, the sort path (parallel arcs, self-loops, unsorted
+    # rows, zero weights) and the error checks are the same as from pageable
+    # memory
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    rng = np.random.default_rng(11)
+    for i in range(16):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        gp = [pin(a) for a in g]
+        orp, ocol, ow = oracle.contract(*g, np.arange(n, dtype=np.int32), n)
+        with mc.Graph(*gp) as G:
+            rp, col, w = G.export()
+            assert (rp == orp).all() and (col == ocol).all() and (w == ow).all()
+            assert G.min_cut().lam == oracle.brute_force(*g)[0]
+    g = graphgen.rhg(2, 1 << 14, 16.0)
+    ref = oracle.noi(*g)[0]
+    with mc.Graph(pin(g[0]), pin(g[1])) as G:
+        assert G.min_cut().lam == ref
+    with mc.Graph(*[pin(a) for a in g]) as G:
+        assert G.min_cut().lam == ref
+    bad = [pin(a) for a in (np.array([0, 1, 1], dtype=np.int32), np.array([1], dtype=np.int32),
+                            np.array([1], dtype=np.int32))]
+    with pytest.raises(mc.MinCutError):
+        mc.Graph(*bad)
+    bad[1][0] = 7  # out of range
     with pytest.raises(mc.MinCutError):
         mc.Graph(*bad)
 
