@@ -80,7 +80,14 @@ typedef struct mc_options {
                                 vertices and 64 arcs per vertex, its remaining
                                 rounds run in one single-warp launch; 0 = the
                                 default (256), < 0 = never; at most 4096       */
-    int32_t reserved_;       /* must be 0                                       */
+    int32_t approx_milli;    /* 0 = exact (default).  1..500: Matula's
+                                (2+eps)-approximation (Sec. 2.2, 3.1.1): each
+                                round unites at lambda-hat = min(best cut,
+                                ceil(approx_milli * delta / 1000)), i.e.
+                                (1/2 - eps) * delta with eps = 1/2 -
+                                approx_milli / 1000; the result is the weight
+                                of a real cut, at most 1000 / approx_milli
+                                times lambda                                   */
 } mc_options;
 
 /* Per-call statistics (all optional). The ms_* phase times come from CUDA events

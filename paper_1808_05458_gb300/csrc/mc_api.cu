@@ -334,8 +334,27 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
 
     // Alg. 2's loop from `cur`, contracting into the free buffer of Ga / Gb;
     // lowers lam and records sides through w.orig
+    //
+    // thr is the bound the round's tests and scans unite at (the value of
+    // st->lam on the device): lam itself, or in the approximation mode
+    // Matula's min(lam, ceil(approx_milli * delta / 1000)) with delta the
+    // minimum degree of the current graph.  A scan whose alpha falls below
+    // thr has found a real cut, which lowers lam as well.
     auto exact_loop = [&](DevGraph cur, DevGraph *nxt) -> int {
     int guard = 0;
+    i64 delta_cur = g->delta0;
+    if (o.approx_milli > 0 && cur.rp != g->G0.rp && cur.n >= 2) {
+        MC_TRY(min_degree(cur, w, s));
+        MC_TRY(status_read(w, s));
+        delta_cur = w.h_st->mindeg;
+    }
+    auto threshold = [&]() -> i64 {
+        if (o.approx_milli <= 0) return lam;
+        const i64 a = o.approx_milli;
+        i64 t = delta_cur / 1000 * a + (delta_cur % 1000 * a + 999) / 1000;  // ceil(a * delta / 1000)
+        if (t < 1) t = 1;
+        return t < lam ? t : lam;
+    };
     while (cur.n >= 2 && lam > 0) {
         if (++guard > 4 * n0 + 64) return MC_EINTERNAL;
         // a small remainder: its rounds in one single-warp launch
@@ -352,15 +371,16 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             break;
         }
         cfg.round = rounds + guard;
+        i64 thr = threshold();
         MC_TRY(union_find_init(w.par, cur.n, s));
-        MC_TRY(round_reset(w, lam, s));
+        MC_TRY(round_reset(w, thr, s));
         // PR1/PR2 and the degree-2 rule on the input graph pass nothing when
         // every weight is below lambda-hat and half of delta and no row has
         // two arcs (unit-weight graphs with delta >= 3): skipped there
-        const bool pr12_idle = cur.rp == g->G0.rp && g->wmax0 < lam && 2 * g->wmax0 <= g->delta0 &&
+        const bool pr12_idle = cur.rp == g->G0.rp && g->wmax0 < thr && 2 * g->wmax0 <= g->delta0 &&
                                g->two_arc_rows0 == 0;
         if (o.pr_level > 0 && !pr12_idle) {
-            MC_TRY(pr_tests_budget(cur, w, lam, 1, o.pr_level < 2 ? o.pr_level : 2, 64, s));
+            MC_TRY(pr_tests_budget(cur, w, thr, 1, o.pr_level < 2 ? o.pr_level : 2, 64, s));
             bytes += cur.arcs * 16;
         }
         ph.mark(&S.ms_pr);
@@ -369,7 +389,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         auto scan_round = [&](int budget, i64 *unions_out) -> int {
             ScanConfig c2 = cfg;
             c2.budget = budget;
-            c2.lam_hint = lam;
+            c2.lam_hint = thr;
             MC_CUDA(cudaEventRecord(ka, s));
             MC_TRY(capforest_parallel(cur, w, c2, s));
             MC_CUDA(cudaEventRecord(kb, s));
@@ -388,9 +408,10 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
                         (long long)st.scans, (long long)st.scanned_verts, (long long)st.scanned_arcs,
                         (long long)st.blacklisted, (long long)st.lam, t);
             bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
-            if (st.lam < lam && st.best_scan > 0) {
+            if (st.lam < thr && st.best_scan > 0) {
                 MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
                 lam = st.lam;
+                thr = st.lam;
             }
             *unions_out = st.unions;
             return MC_OK;
@@ -400,7 +421,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         ph.mark(&S.ms_capforest);
         // a poor round: the triangle tests PR3/PR4 add their unions
         if (o.pr_level >= 3 && unions * 4 < cur.n) {
-            MC_TRY(pr_tests_budget(cur, w, lam, 3, o.pr_level, 64, s));
+            MC_TRY(pr_tests_budget(cur, w, thr, 3, o.pr_level, 64, s));
             MC_TRY(status_read(w, s));
             unions = w.h_st->unions;
             bytes += cur.arcs * 16;
@@ -412,18 +433,19 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             ph.mark(&S.ms_capforest);
         }
         if (unions == 0) {
-            const i64 lam_before = lam;
+            const i64 thr_before = thr;
             ScanConfig cf = cfg;
-            cf.lam_hint = lam;
+            cf.lam_hint = thr;
             MC_TRY(capforest_full(cur, w, cf, s));
             MC_TRY(status_read(w, s));
             const Status st = *w.h_st;
             S.scanned_arcs += st.scanned_arcs;
             S.scanned_verts += st.scanned_verts;
             bytes += st.scanned_arcs * 8 + st.scanned_verts * 24;
-            if (st.lam < lam && st.best_scan > 0) {
+            if (st.lam < thr && st.best_scan > 0) {
                 MC_TRY(side_from_scan(w, n0, st.best_scan, st.best_len, s));
                 lam = st.lam;
+                thr = st.lam;
             }
             unions = st.unions;
             ++fallbacks;
@@ -432,7 +454,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
                         (long long)unions, (long long)lam);
             if (unions == 0) {
                 ph.mark(&S.ms_capforest);
-                if (lam < lam_before) continue;  // lambda-hat dropped inside the scan: rescan
+                if (thr < thr_before) continue;  // lambda-hat dropped inside the scan: rescan
                 set_error_detail("full CAPFOREST scan marked no edge");
                 return MC_EINTERNAL;
             }
@@ -450,6 +472,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             lam = w.h_st->mindeg;
             MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
         }
+        delta_cur = w.h_st->mindeg;
         ph.mark(&S.ms_contract);
         if (verbose)
             fprintf(stderr, "[mc]   contract -> n=%d arcs=%lld emitted=%lld (%.3f ms) lam=%lld\n", nxt->n,
@@ -543,7 +566,7 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out, uint32_t
     if (!g || !lambda_out) return MC_EINVAL;
     mc_options o;
     if (opt) o = *opt; else mc_options_default(&o);
-    if (o.pr_level < 0 || o.pr_level > 4 || o.reserved_ != 0) return MC_EINVAL;
+    if (o.pr_level < 0 || o.pr_level > 4 || o.approx_milli < 0 || o.approx_milli > 500) return MC_EINVAL;
     cudaStream_t s = pick_stream(g, opt);
     SolveOut so;
     int rc = solve_impl(g, o, s, so);

@@ -346,9 +346,49 @@ def test_tail_solver_sizes(mc, tail):
 def test_tail_option_checks(mc):
     g = graphgen.cycle(10, 3)
     with mc.Graph(*g) as G:
-        with pytest.raises(mc.MinCutError):
-            G.min_cut(mc.options(reserved_=1))
+        for bad in (-1, 501):
+            with pytest.raises(mc.MinCutError):
+                G.min_cut(mc.options(approx_milli=bad))
         assert G.min_cut(mc.options(tail_vertices=1 << 20)).lam == 6
+
+
+def _approx_ok(mc, g, res, lam, a):
+    # Matula's guarantee: a real cut, at most 1000 / a times lambda
+    n = len(g[0]) - 1
+    assert lam <= res.lam and res.lam * a <= lam * 1000, (lam, res.lam, a)
+    side = res.side(n)
+    assert side[0] == 0 and 0 < side.sum() < n
+    assert oracle.cut_weight(*g, side) == res.lam
+
+
+def test_approx_mode_tiny(mc):
+    rng = np.random.default_rng(21)
+    for i in range(300):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        lam = oracle.brute_force(*g)[0]
+        with mc.Graph(*g) as G:
+            for a in (500, 400, 250, 1):
+                _approx_ok(mc, g, G.min_cut(mc.options(approx_milli=a, seed=i)), lam, a)
+
+
+@pytest.mark.parametrize("a", [500, 450, 300])
+def test_approx_mode_workloads(mc, a):
+    # planted (lambda = 8 below delta), RHG (lambda = delta), a weighted
+    # R-MAT core, the LP bound in front, and a disconnected graph (0)
+    cases = [(graphgen.planted(1), {}), (graphgen.rhg(2, 1 << 16, 32.0), {}),
+             (graphgen.rmat_kcore(1, scale=15), {}), (graphgen.rhg(4, 1 << 15, 32.0), {"bound": 1})]
+    for g, kw in cases:
+        lam = oracle.noi(*g)[0]
+        with mc.Graph(*g) as G:
+            exact = G.min_cut(mc.options(**kw)).lam
+            res = G.min_cut(mc.options(approx_milli=a, **kw))
+        assert exact == lam
+        _approx_ok(mc, g, res, lam, a)
+    g = graphgen.from_edges(6, np.array([0, 1, 3, 4]), np.array([1, 2, 4, 5]), np.array([5, 5, 5, 5]))
+    with mc.Graph(*g) as G:
+        assert G.min_cut(mc.options(approx_milli=a)).lam == 0
 
 
 @pytest.mark.parametrize("seed", range(10))
