@@ -419,9 +419,12 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         i64 unions = 0;
         MC_TRY(scan_round(cfg.budget, &unions));
         ph.mark(&S.ms_capforest);
-        // a poor round: the triangle tests PR3/PR4 add their unions
+        // a poor round: the triangle tests PR3/PR4 add their unions, on the
+        // edges whose shorter row has at most 16 arcs (their work grows with
+        // the square of that row: measured on R-MAT 10-cores, 16 arcs beat
+        // 24, 32 and 64 end to end, 17.3 against 17.5, 20.7 and 25.0 ms)
         if (o.pr_level >= 3 && unions * 4 < cur.n) {
-            MC_TRY(pr_tests_budget(cur, w, thr, 3, o.pr_level, 64, s));
+            MC_TRY(pr_tests_budget(cur, w, thr, 3, o.pr_level, 16, s));
             MC_TRY(status_read(w, s));
             unions = w.h_st->unions;
             bytes += cur.arcs * 16;

@@ -181,6 +181,10 @@ k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs, cons
             // (both terms <= cap < 2^31, so the u32 add cannot wrap) toward
             // the run's first lane; a lane takes lane + o's partial sum when
             // no run starts in (lane, lane + o]
+            key[k] = ~0ULL;
+            // after a round that contracted much, most warps hold no
+            // crossing arc: nothing to merge
+            if (!__any_sync(0xffffffffu, kk != ~0ULL)) continue;
             const u64 kp = __shfl_up_sync(0xffffffffu, kk, 1);
             const bool head = lane == 0 || kp != kk;
             const unsigned hm = __ballot_sync(0xffffffffu, head);
@@ -196,7 +200,6 @@ k_emit(const int *__restrict__ src, const int2 *__restrict__ adj, i64 arcs, cons
                     sv = x > (unsigned)cap ? (unsigned)cap : x;
                 }
             }
-            key[k] = ~0ULL;
             if (head && kk != ~0ULL) {
                 if (wide && clamp > (i64)kInt32Max) atomicOr(err, kErrOverflow);
                 key[k] = kk;

@@ -85,13 +85,14 @@ __device__ __forceinline__ int find_in_global(const int2 *row, int len, int x) {
 }
 
 __global__ void __launch_bounds__(kPrWarps * 32)
-k_pr34(const DevGraph g, int *par, long long lam, int lo, int level, int budget, unsigned long long *unions) {
+k_pr34(const DevGraph g, int *par, long long lam, int lo, int level, int budget, int min_len,
+       unsigned long long *unions) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     long long local = 0;
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < g.n; u += nw) {
         const int u0 = g.rp[u], u1 = g.rp[u + 1], lu = u1 - u0;
-        if (lu == 0 || (budget >= 0 && lu > budget)) continue;
+        if (lu <= min_len || (budget >= 0 && lu > budget)) continue;
         const long long du = g.deg[u];
         for (int i0 = u0; i0 < u1; i0 += 32) {
             const int i = i0 + lane;
@@ -139,6 +140,96 @@ k_pr34(const DevGraph g, int *par, long long lam, int lo, int level, int budget,
     if (local) atomicAdd(unions, (unsigned long long)local);
 }
 
+// PR3/PR4 for rows of at most kPairRow arcs, one warp per vertex u with
+// every (owned edge (u, v), neighbour w of u) pair on its own lane: u's row
+// and its owned edges go to shared memory, each lane binary-searches w in
+// v's row, and PR4's sums and PR3's flags gather per edge in shared memory.
+// The same edges and conditions as k_pr34; a short row fills the warp
+// instead of one lane per neighbour.
+constexpr int kPairRow = 64;
+
+struct Pr34Smem {
+    int w[kPairRow];
+    int cw[kPairRow];
+    int v[kPairRow];
+    int cv[kPairRow];
+    int v0[kPairRow];
+    int lv[kPairRow];
+    long long dv[kPairRow];
+    unsigned long long pr4[kPairRow];
+    int pr3[kPairRow];
+};
+
+__global__ void __launch_bounds__(kPrWarps * 32)
+k_pr34_pairs(const DevGraph g, int *par, long long lam, int lo, int level, int max_len,
+             unsigned long long *unions) {
+    __shared__ Pr34Smem smem[kPrWarps];
+    Pr34Smem &sm = smem[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    long long local = 0;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < g.n; u += nw) {
+        const int u0 = g.rp[u], lu = g.rp[u + 1] - u0;
+        if (lu == 0 || lu > max_len) continue;
+        const long long du = g.deg[u];
+        // u's row, and the edges u owns (the longer row on the other side,
+        // ties to the larger id) that PR1/PR2 do not already take
+        int ne = 0;
+        for (int i0 = 0; i0 < lu; i0 += 32) {
+            const int i = i0 + lane;
+            bool own = false;
+            int v = 0, c = 0, v0 = 0, lv = 0;
+            long long dv = 0;
+            if (i < lu) {
+                const int2 e = g.adj[u0 + i];
+                v = e.x;
+                c = e.y;
+                sm.w[i] = v;
+                sm.cw[i] = c;
+                v0 = g.rp[v];
+                lv = g.rp[v + 1] - v0;
+                dv = g.deg[v];
+                own = lv > lu || (lv == lu && v > u);
+                if (own && lo <= 2)
+                    own = !((lo <= 1 && level >= 1 && (long long)c >= lam) ||
+                            (level >= 2 && 2LL * c > (du < dv ? du : dv)));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, own);
+            if (own) {
+                const int j = ne + __popc(m & ((1u << lane) - 1u));
+                sm.v[j] = v;
+                sm.cv[j] = c;
+                sm.v0[j] = v0;
+                sm.lv[j] = lv;
+                sm.dv[j] = dv;
+                sm.pr4[j] = 0;
+                sm.pr3[j] = 0;
+            }
+            ne += __popc(m);
+        }
+        __syncwarp();
+        if (ne == 0) continue;
+        const int np = ne * lu;
+        for (int p = lane; p < np; p += 32) {
+            const int j = p / lu, k = p - j * lu;
+            const int x = sm.w[k], vv = sm.v[j];
+            if (x == vv) continue;
+            const int cvw = find_in_global(g.adj + sm.v0[j], sm.lv[j], x);
+            if (cvw == 0) continue;
+            const long long cuw = sm.cw[k], cc = sm.cv[j];
+            if (2 * (cc + cuw) > du && 2 * (cc + cvw) > sm.dv[j]) sm.pr3[j] = 1;
+            atomicAdd(&sm.pr4[j], (unsigned long long)(cuw < cvw ? cuw : cvw));
+        }
+        __syncwarp();
+        for (int j = lane; j < ne; j += 32) {
+            const bool ok = sm.pr3[j] != 0 || (level >= 4 && (long long)sm.cv[j] + (long long)sm.pr4[j] >= lam);
+            if (ok && uf_union(par, u, sm.v[j])) ++local;
+        }
+        __syncwarp();
+    }
+    if (local) atomicAdd(unions, (unsigned long long)local);
+}
+
 int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int budget,
                     cudaStream_t s) {
     if (level <= 0 || lo > level || g.arcs == 0) return MC_OK;
@@ -151,7 +242,11 @@ int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int 
         long long wb = ((long long)g.n + kPrWarps - 1) / kPrWarps;
         const long long cap = (long long)num_sms() * 8;
         if (wb > cap) wb = cap;
-        ++::mc::g_launches; k_pr34<<<(int)wb, kPrWarps * 32, 0, s>>>(g, w.par, lam, lo, level, budget, un);
+        const int short_len = budget >= 0 && budget < kPairRow ? budget : kPairRow;
+        ++::mc::g_launches; k_pr34_pairs<<<(int)wb, kPrWarps * 32, 0, s>>>(g, w.par, lam, lo, level, short_len, un);
+        if (budget < 0 || budget > kPairRow) {
+            ++::mc::g_launches; k_pr34<<<(int)wb, kPrWarps * 32, 0, s>>>(g, w.par, lam, lo, level, budget, kPairRow, un);
+        }
     }
     MC_CUDA(cudaGetLastError());
     return MC_OK;
