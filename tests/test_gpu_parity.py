@@ -637,6 +637,17 @@ def test_rmat_kcore_scale20(mc):
     check_cut(mc, g, res, ref)
 
 
+@pytest.mark.parametrize("k,order", [(50, 0), (100, 1)])
+def test_rmat_dense_kcores(mc, k, order):
+    # deeper k-cores of a Kronecker (R-MAT) graph, as the paper's real-world
+    # k-core inputs, in both bucket orders
+    g = graphgen.rmat_kcore(2, scale=18, k=k)
+    ref, _, _ = oracle.noi(*g)
+    with mc.Graph(*g) as G:
+        res = G.min_cut(mc.options(pq_order=order))
+    check_cut(mc, g, res, ref)
+
+
 def test_capforest_full_scan_safe_and_progresses(mc):
     # Alg. 3: a full scan at lambda-hat <= delta unites at least one edge
     # unless alpha lowered lambda-hat during the scan (Sec. 2.2), and every
