@@ -59,3 +59,33 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.mc_graph_create(1, rp.ctypes.data, None, None, 0, ctypes.byref(h)) == -1
     assert lib.mc_min_cut(None, None, None, None, None) == -1
     assert lib.mc_graph_destroy(None) == -1
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    # the ctypes structures of the binding against the C compiler's view of
+    # include/mc.h: size and every field offset
+    import shutil
+    import subprocess
+    from paper_1808_05458_gb300 import mincut
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mc_options": mincut.McOptions, "mc_stats": mincut.McStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, fname, val = line.split()
+        got[(cname, fname)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
