@@ -87,7 +87,8 @@ typedef struct mc_options {
                                 (1/2 - eps) * delta with eps = 1/2 -
                                 approx_milli / 1000; the result is the weight
                                 of a real cut, at most 1000 / approx_milli
-                                times lambda                                   */
+                                times lambda.  mc_min_cut only: the batched
+                                solver always solves exactly                   */
 } mc_options;
 
 /* Per-call statistics (all optional). The ms_* phase times come from CUDA events
