@@ -540,6 +540,22 @@ def test_batch_small(mc):
     _check_batch_sides(b, lam, bits, boff, range(48))
 
 
+def test_batch_sharded_ranges(mc):
+    # the per-rank ranges of a sharded batch, each solved by its own
+    # mc_batch_min_cut call, give the whole batch's lambdas
+    from paper_1808_05458_gb300 import shard
+    b = graphgen.batch(8, G=40)
+    full = mc.batch_min_cut(*b)[0]
+    for world in (1, 3, 7):
+        bounds = shard.shard_bounds(b[3], b[4], world)
+        parts = [mc.batch_min_cut(*shard.sub_batch(b, int(bounds[r]), int(bounds[r + 1])))[0]
+                 for r in range(world) if bounds[r + 1] > bounds[r]]
+        assert (np.concatenate(parts) == full).all()
+    lam = shard.sharded_batch_min_cut(b, 0, 1, lambda x: [x])
+    assert (lam == full).all()
+    assert all(full[k] == oracle.noi(*graphgen.batch_graph(b, k))[0] for k in range(40))
+
+
 def test_batch_graph_replay(mc):
     # the persistent launch is captured once per batch layout and replayed:
     # repeated calls, then another layout, then the first again
