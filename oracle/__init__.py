@@ -73,6 +73,8 @@ def _load():
         lib.orc_stoer_wagner.restype = i64
         lib.orc_noi.argtypes = [i32, I32P, I32P, I32P, ctypes.c_int, u64, U8P, I32P]
         lib.orc_noi.restype = i64
+        lib.orc_matula.argtypes = [i32, I32P, I32P, I32P, ctypes.c_int, u64, U8P, I32P]
+        lib.orc_matula.restype = i64
         lib.orc_contract.argtypes = [i32, I32P, I32P, I32P, I32P, i32, I64P, I32P, I64P]
         lib.orc_contract.restype = i64
         lib.orc_label_prop.argtypes = [i32, I32P, I32P, I32P, ctypes.c_int, u64, I32P]
@@ -152,6 +154,20 @@ def noi(rp, col, w, capped: bool = True, seed: int = 0):
                                  _p(w, ctypes.c_int32), 1 if capped else 0,
                                  ctypes.c_uint64(seed & (2**64 - 1)),
                                  _p(side, ctypes.c_uint8), _p(rounds, ctypes.c_int32)), "noi")
+    return int(lam), side, int(rounds[0])
+
+
+def matula(rp, col, w, approx_milli: int, seed: int = 0):
+    """(cut, side, rounds) by Matula's approximation: the NOI loop marking at
+    ceil(approx_milli * delta / 1000) each round; lambda <= cut <=
+    1000 / approx_milli * lambda."""
+    n, rp, col, w = _csr(rp, col, w)
+    side = np.zeros(n, dtype=np.uint8)
+    rounds = np.zeros(1, dtype=np.int32)
+    lam = _check(_load().orc_matula(n, _p(rp, ctypes.c_int32), _p(col, ctypes.c_int32),
+                                    _p(w, ctypes.c_int32), int(approx_milli),
+                                    ctypes.c_uint64(seed & (2**64 - 1)),
+                                    _p(side, ctypes.c_uint8), _p(rounds, ctypes.c_int32)), "matula")
     return int(lam), side, int(rounds[0])
 
 

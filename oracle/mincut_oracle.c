@@ -19,6 +19,9 @@
  *                      with the priority queue capped at lambda-hat
  *                      (Sec. 3.1.2, Lemma 1) and contract (Sec. 2.1), keeping
  *                      the side as in Sec. 3.3.
+ *   orc_matula         Matula's (2+eps)-approximation: the same loop marking
+ *                      at (1/2 - eps) times the minimum degree each round
+ *                      (Sec. 2.2, Sec. 3.1.1).
  *   orc_contract       Sec. 2.1 edge contraction G/(u,v) applied to every
  *                      block of a vertex labelling at once.
  *   orc_label_prop     label propagation as used by VieCut (Sec. 2.3); the
@@ -35,7 +38,9 @@
  * Pins (tests/test_oracle_*.py): closed forms (K_n, C_n, trees, planted
  * cliques, disconnected graphs), brute force vs Stoer-Wagner vs NOI on
  * thousands of random tiny graphs, capped vs uncapped NOI, contraction
- * preserving the weight of every cut that does not split a block.
+ * preserving the weight of every cut that does not split a block; Matula's
+ * guarantee lambda <= cut <= lambda / (1/2 - eps) against brute force, its
+ * side re-weighed, and exactness wherever lambda = delta.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -469,8 +474,14 @@ i64 orc_contract(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
 /* A round that marks nothing must have lowered lambda-hat (Sec. 2.2: a full   */
 /* CAPFOREST with lambda-hat <= delta marks an edge unless lambda-hat dropped  */
 /* inside the round); otherwise the oracle reports ORC_ENOPROGRESS.            */
-i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
-            int capped, u64 seed, uint8_t *side_out, int32_t *rounds_out)
+/*                                                                            */
+/* With approx_milli = a in [1, 500] the same loop is Matula's                */
+/* (2+eps)-approximation as Sec. 3.1.1 describes it: each round marks at the  */
+/* threshold t = min(lambda-hat, ceil(a * delta / 1000)), (1/2 - eps) times   */
+/* the current minimum degree, instead of at lambda-hat; lambda-hat keeps the */
+/* best real cut (degrees, alpha values below t).  a = 0 is the exact loop.   */
+static i64 noi_loop(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                    int capped, int approx_milli, u64 seed, uint8_t *side_out, int32_t *rounds_out)
 {
     ograph g;
     int *map = NULL, *lab = NULL, *par = NULL, *scanned = NULL, *order = NULL;
@@ -511,7 +522,16 @@ i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
     while (g.n >= 2 && lam > 0) {
         oheap h;
         int nS = 0, start, x, nc;
-        i64 alpha = 0, marked = 0, lam_at_start = lam;
+        i64 alpha = 0, marked = 0, thr = lam, thr_at_start;
+        if (approx_milli > 0) {
+            i64 dmin = deg[0], t;
+            for (v = 1; v < g.n; ++v)
+                if (deg[v] < dmin) dmin = deg[v];
+            t = dmin / 1000 * approx_milli + (dmin % 1000 * approx_milli + 999) / 1000;
+            if (t < 1) t = 1;
+            if (t < thr) thr = t;
+        }
+        thr_at_start = thr;
         if (oh_init(&h, g.n) != ORC_OK) { rc = ORC_ENOMEM; goto done; }
         for (v = 0; v < g.n; ++v) { par[v] = v; scanned[v] = 0; r[v] = 0; }
         start = (int)(orc_splitmix64(seed ^ (u64)rounds) % (u64)g.n);
@@ -521,9 +541,10 @@ i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
             x = oh_pop(&h);
             alpha += deg[x] - 2 * r[x];
             order[nS++] = x;
-            if (nS < g.n && alpha < lam) {
+            if (nS < g.n && alpha < thr) {
                 int k;
                 lam = alpha;
+                thr = alpha;
                 for (v = 0; v < g.n; ++v) lab[v] = 0;
                 for (k = 0; k < nS; ++k) lab[order[k]] = 1;
                 for (v = 0; v < n; ++v) best_side[v] = (uint8_t)lab[map[v]];
@@ -532,10 +553,10 @@ i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
                 int y = g.col[a];
                 i64 c = g.w[a];
                 if (scanned[y]) continue;
-                if (r[y] < lam && lam <= r[y] + c) marked += uf_union(par, x, y);
+                if (r[y] < thr && thr <= r[y] + c) marked += uf_union(par, x, y);
                 r[y] += c;
                 if (capped) {
-                    i64 k = r[y] < lam ? r[y] : lam;
+                    i64 k = r[y] < thr ? r[y] : thr;
                     oh_raise(&h, y, k);
                 } else {
                     oh_raise(&h, y, r[y]);
@@ -547,7 +568,7 @@ i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
         ++rounds;
         if (lam == 0) break;
         if (marked == 0) {
-            if (lam < lam_at_start) continue;
+            if (thr < thr_at_start) continue;
             rc = ORC_ENOPROGRESS;
             goto done;
         }
@@ -588,6 +609,21 @@ done:
     free(r); free(deg); free(best_side);
     og_free(&g);
     return rc == ORC_OK ? lam : rc;
+}
+
+i64 orc_noi(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
+            int capped, u64 seed, uint8_t *side_out, int32_t *rounds_out)
+{
+    return noi_loop(n, rp, col, w, capped, 0, seed, side_out, rounds_out);
+}
+
+/* Matula's (2+eps)-approximation (Sec. 2.2, Sec. 3.1.1): a real cut of      */
+/* weight at most 1000 / approx_milli times lambda; approx_milli in [1, 500]. */
+i64 orc_matula(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
+               int approx_milli, u64 seed, uint8_t *side_out, int32_t *rounds_out)
+{
+    if (approx_milli < 1 || approx_milli > 500) return ORC_EINVAL;
+    return noi_loop(n, rp, col, w, 1, approx_milli, seed, side_out, rounds_out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -411,3 +411,41 @@ def test_gnn_reference_polarity_invariant():
     side = (np.arange(n) % 3 == 0).astype(np.int64)
     p = gnn.glorot(4)
     assert gnn.loss_only(p, *g, side) == gnn.loss_only(p, *g, 1 - side)
+
+
+# ---------------------------------------------------- Matula approximation
+@pytest.mark.parametrize("a", [500, 400, 250, 1])
+def test_matula_guarantee_vs_brute_force(a):
+    # Sec. 3.1.1: marking at (1/2 - eps) * delta returns a real cut within
+    # a factor 1 / (1/2 - eps) = 1000 / a of lambda
+    rng = np.random.default_rng(777 + a)
+    loose = 0
+    for i in range(800):
+        n, g = _random_tiny(rng, i)
+        bf, _ = oracle.brute_force(*g)
+        cut, side, _ = oracle.matula(*g, a, seed=i)
+        assert bf <= cut and cut * a <= bf * 1000, (i, bf, cut, a)
+        assert side_ok(side, n) and oracle.cut_weight(*g, side) == cut
+        loose += cut > bf
+    if a <= 250:
+        assert loose > 0  # the threshold really is lower than lambda-hat
+
+
+def test_matula_exact_where_lambda_is_delta():
+    # the answer never exceeds delta, so it is exact whenever lambda = delta
+    for n, wt in [(2, 3), (7, 1), (30, 2)]:
+        for a in (500, 100):
+            assert oracle.matula(*graphgen.complete(n, wt), a)[0] == (n - 1) * wt
+            if n >= 3:
+                assert oracle.matula(*graphgen.cycle(n, wt), a)[0] == 2 * wt
+    g = graphgen.rhg(1, 1 << 12, 16.0)
+    lam = oracle.noi(*g)[0]
+    if lam == int(oracle.degrees(*g).min()):
+        assert oracle.matula(*g, 450)[0] == lam
+
+
+def test_matula_rejects_bad_settings():
+    g = graphgen.cycle(5)
+    for a in (0, 501, -3):
+        with pytest.raises(Exception):
+            oracle.matula(*g, a)
