@@ -75,6 +75,8 @@ def _load():
         lib.orc_noi.restype = i64
         lib.orc_matula.argtypes = [i32, I32P, I32P, I32P, ctypes.c_int, u64, U8P, I32P]
         lib.orc_matula.restype = i64
+        lib.orc_capforest_round.argtypes = [i32, I32P, I32P, I32P, i64, i32, I32P]
+        lib.orc_capforest_round.restype = i64
         lib.orc_contract.argtypes = [i32, I32P, I32P, I32P, I32P, i32, I64P, I32P, I64P]
         lib.orc_contract.restype = i64
         lib.orc_label_prop.argtypes = [i32, I32P, I32P, I32P, ctypes.c_int, u64, I32P]
@@ -155,6 +157,17 @@ def noi(rp, col, w, capped: bool = True, seed: int = 0):
                                  ctypes.c_uint64(seed & (2**64 - 1)),
                                  _p(side, ctypes.c_uint8), _p(rounds, ctypes.c_int32)), "noi")
     return int(lam), side, int(rounds[0])
+
+
+def capforest_round(rp, col, w, lam: int, start: int):
+    """(lambda-hat after the scan, labels) of one capped CAPFOREST scan from
+    start: labels[v] = the smallest vertex of v's block of marked edges."""
+    n, rp, col, w = _csr(rp, col, w)
+    lab = np.zeros(n, dtype=np.int32)
+    out = _check(_load().orc_capforest_round(n, _p(rp, ctypes.c_int32), _p(col, ctypes.c_int32),
+                                             _p(w, ctypes.c_int32), int(lam), int(start),
+                                             _p(lab, ctypes.c_int32)), "capforest_round")
+    return int(out), lab
 
 
 def matula(rp, col, w, approx_milli: int, seed: int = 0):

@@ -19,6 +19,8 @@
  *                      with the priority queue capped at lambda-hat
  *                      (Sec. 3.1.2, Lemma 1) and contract (Sec. 2.1), keeping
  *                      the side as in Sec. 3.3.
+ *   orc_capforest_round  one capped CAPFOREST scan (Appendix Alg. 3) and the
+ *                      unions it marks: one round of orc_noi on its own.
  *   orc_matula         Matula's (2+eps)-approximation: the same loop marking
  *                      at (1/2 - eps) times the minimum degree each round
  *                      (Sec. 2.2, Sec. 3.1.1).
@@ -624,6 +626,59 @@ i64 orc_matula(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
 {
     if (approx_milli < 1 || approx_milli > 500) return ORC_EINVAL;
     return noi_loop(n, rp, col, w, 1, approx_milli, seed, side_out, rounds_out);
+}
+
+/* One capped CAPFOREST scan (Appendix Alg. 3) from `start` against the      */
+/* bound lam: the steps of one orc_noi round, on its own.  lab_out[v] = the   */
+/* smallest vertex of v's block of marked edges; returns lambda-hat after the */
+/* scan (lowered by alpha while the scanned set is a proper subset).          */
+i64 orc_capforest_round(int n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                        i64 lam, int start, int32_t *lab_out)
+{
+    ograph g;
+    oheap h;
+    int *par = NULL, *scanned = NULL;
+    i64 *r = NULL, *deg = NULL, alpha = 0;
+    int v, nS = 0, rc = ORC_OK;
+    if (n < 1 || start < 0 || start >= n || lam < 0) return ORC_EINVAL;
+    if (check_csr(n, rp, col) != ORC_OK) return ORC_EINVAL;
+    if (og_from_csr(n, rp, col, w, &g) != ORC_OK) return ORC_ENOMEM;
+    par = (int *)malloc(sizeof(int) * (size_t)n);
+    scanned = (int *)calloc((size_t)n, sizeof(int));
+    r = (i64 *)calloc((size_t)n, sizeof(i64));
+    deg = (i64 *)calloc((size_t)n, sizeof(i64));
+    if (!par || !scanned || !r || !deg || oh_init(&h, n) != ORC_OK) {
+        free(par); free(scanned); free(r); free(deg);
+        og_free(&g);
+        return ORC_ENOMEM;
+    }
+    for (v = 0; v < n; ++v) {
+        i64 a;
+        par[v] = v;
+        for (a = g.rp[v]; a < g.rp[v + 1]; ++a) deg[v] += g.w[a];
+    }
+    oh_raise(&h, start, 0);
+    while (h.size > 0) {
+        i64 a;
+        const int x = oh_pop(&h);
+        alpha += deg[x] - 2 * r[x];
+        ++nS;
+        if (nS < n && alpha < lam) lam = alpha;
+        for (a = g.rp[x]; a < g.rp[x + 1]; ++a) {
+            const int y = g.col[a];
+            const i64 c = g.w[a];
+            if (scanned[y]) continue;
+            if (r[y] < lam && lam <= r[y] + c) uf_union(par, x, y);
+            r[y] += c;
+            oh_raise(&h, y, r[y] < lam ? r[y] : lam);
+        }
+        scanned[x] = 1;
+    }
+    for (v = 0; v < n; ++v) lab_out[v] = uf_find(par, v);
+    oh_free(&h);
+    free(par); free(scanned); free(r); free(deg);
+    og_free(&g);
+    return rc == ORC_OK ? lam : rc;
 }
 
 /* ------------------------------------------------------------------------ */

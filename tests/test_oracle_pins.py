@@ -449,3 +449,70 @@ def test_matula_rejects_bad_settings():
     for a in (0, 501, -3):
         with pytest.raises(Exception):
             oracle.matula(*g, a)
+
+
+# ------------------------------------------------- one CAPFOREST round
+def test_capforest_round_safe_and_progresses():
+    # Lemma 1 / Lemma 2: the unions of one capped scan keep
+    # min(lambda-hat, lambda(G/U)) = lambda(G); with lambda-hat <= delta and
+    # lambda-hat unchanged by the scan, at least one edge is marked (Sec. 2.2)
+    rng = np.random.default_rng(4242)
+    for i in range(1500):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        lam, _ = oracle.brute_force(*g)
+        delta = int(oracle.degrees(*g).min())
+        for bound in {delta, lam}:
+            if bound <= 0:
+                continue
+            out, lab = oracle.capforest_round(*g, bound, i % n)
+            assert lam <= out <= bound
+            roots, lab2 = np.unique(lab, return_inverse=True)
+            assert (lab[roots] == roots).all() and (lab <= np.arange(n)).all()
+            if len(roots) >= 2:
+                crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+                lam_c, _ = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))
+                assert min(out, lam_c) == lam, (i, bound, out, lam_c, lam)
+            else:
+                assert out == lam
+            if out == bound and lam > 0:
+                assert len(roots) < n
+
+
+def _noi_by_rounds(g, seed):
+    # orc_noi's loop rebuilt from single rounds: the same starts, the same
+    # contraction (blocks numbered by their smallest member), the same bound
+    cur = g
+    lam = int(oracle.degrees(*g).min())
+    rounds = 0
+    while len(cur[0]) - 1 >= 2 and lam > 0:
+        n = len(cur[0]) - 1
+        before = lam
+        start = oracle.splitmix64(seed ^ rounds) % n
+        lam, lab = oracle.capforest_round(*cur, lam, start)
+        rounds += 1
+        if lam == 0:
+            break
+        roots, lab2 = np.unique(lab, return_inverse=True)
+        if len(roots) == n:
+            assert lam < before
+            continue
+        crp, ccol, cw = oracle.contract(*cur, lab2.astype(np.int32), len(roots))
+        cur = (crp.astype(np.int32), ccol, cw.astype(np.int32))
+        if len(roots) >= 2:
+            lam = min(lam, int(oracle.degrees(*cur).min()))
+    return lam, rounds
+
+
+def test_capforest_rounds_compose_to_noi():
+    rng = np.random.default_rng(99)
+    for i in range(400):
+        n, g = _random_tiny(rng, i)
+        if n < 2:
+            continue
+        lam, _, rounds = oracle.noi(*g, seed=i)
+        assert _noi_by_rounds(g, i) == (lam, rounds), i
+    g = graphgen.planted(2, block_n=200, avg_deg=10, cross=3)
+    lam, _, rounds = oracle.noi(*g, seed=7)
+    assert _noi_by_rounds(g, 7) == (lam, rounds)
