@@ -30,6 +30,10 @@
  *
  * Threads and streams: calls on one mc_graph must not overlap; different
  * graphs may be used from different threads on different streams.
+ *
+ * Diagnostics: with the environment variable MC_VERBOSE set, mc_min_cut
+ * prints one line per round (sizes, unions, lambda-hat, phase times) to
+ * stderr; the result does not change.
  */
 #ifndef MC_H
 #define MC_H
