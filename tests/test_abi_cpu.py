@@ -89,3 +89,21 @@ def test_binding_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_constants_match_header():
+    # every #define MC_* integer of include/mc.h that the binding mirrors
+    from paper_1808_05458_gb300 import mincut
+    text = open(os.path.join(ROOT, "include", "mc.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(MC_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)}
+    alias = {"MC_PROPOSER_PARAMS": "PROPOSER_PARAMS"}
+    mirrored = 0
+    for k, v in defs.items():
+        name = alias.get(k, k)
+        if hasattr(mincut, name):
+            assert getattr(mincut, name) == v, k
+            mirrored += 1
+    for k in ("MC_OK", "MC_EINVAL", "MC_ENOMEM", "MC_EOVERFLOW", "MC_PQ_FIFO", "MC_BOUND_LP",
+              "MC_DEVICE_PTRS", "MC_PROPOSER_PARAMS"):
+        assert k in defs and hasattr(mincut, alias.get(k, k)), k
+    assert mirrored >= 15
