@@ -12,7 +12,12 @@ mathematics determine independently:
 * Lemma 1 (capped queue) -- capped and uncapped NOI agree;
 * contraction (Sec. 2.1) preserves the capacity of every cut that keeps each
   block on one side;
-* the published splitmix64 output sequence for seed 1234567.
+* the published splitmix64 output sequence for seed 1234567;
+* hand-derived Padberg-Rinaldi blocks where PR2 and PR3 must fire (and
+  where a one-sided or max-degree variant would not), and hand-derived
+  label-propagation sweeps where synchronous half-sweeps, the parity split
+  and the weighted choice each give a different result from the obvious
+  alternative.
 """
 import json
 import os
@@ -308,6 +313,118 @@ def test_pr1_pr4_closed_forms():
     lab = oracle.pr_tests(*g, 5, 4)
     assert (lab == 0).all()
     assert len(np.unique(oracle.pr_tests(*g, 5, 3))) == 6  # PR3 needs > d/2
+
+
+def _blocks_safe(g, lab, bound):
+    # min(bound, lambda(G / blocks)) = lambda(G): the test's unions are safe
+    lam = oracle.brute_force(*g)[0]
+    roots, lab2 = np.unique(lab, return_inverse=True)
+    if len(roots) == 1:
+        return bound == lam
+    crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+    lam_c = oracle.brute_force(crp.astype(np.int32), ccol, cw.astype(np.int32))[0]
+    return min(bound, lam_c) == lam
+
+
+def test_pr2_fires_on_heavy_edges():
+    # Edges (weight): 0-1 (5), 0-2 (4), 1-2 (4), 1-3 (3), 2-3 (6).
+    # Weighted degrees: d0 = 9, d1 = 12, d2 = 14, d3 = 9; delta = bound = 9,
+    # so PR1 (c >= 9) passes nothing and no vertex has two equal-weight arcs
+    # as its only ones (the degree-2 rule stays out).
+    # PR2, 2c > min(d(u), d(v)):
+    #   0-1: 10 > min(9, 12) = 9   passes (but 10 <= max = 12)
+    #   0-2:  8 > min(9, 14) = 9   fails
+    #   1-2:  8 > min(12, 14) = 12 fails
+    #   1-3:  6 > min(12, 9) = 9   fails
+    #   2-3: 12 > min(14, 9) = 9   passes (but 12 <= max = 14)
+    # Blocks {0, 1} and {2, 3}: labels (smallest member) 0, 0, 2, 2.
+    u = np.array([0, 0, 1, 1, 2])
+    v = np.array([1, 2, 2, 3, 3])
+    c = np.array([5, 4, 4, 3, 6])
+    g = graphgen.from_edges(4, u, v, c)
+    assert list(oracle.degrees(*g)) == [9, 12, 14, 9]
+    assert list(oracle.pr_tests(*g, 9, 1)) == [0, 1, 2, 3]
+    lab = oracle.pr_tests(*g, 9, 2)
+    assert list(lab) == [0, 0, 2, 2]
+    assert _blocks_safe(g, lab, 9)
+
+
+def test_pr3_fires_on_a_triangle_meeting_both_conditions():
+    # Prism: triangles {0, 1, 2} and {3, 4, 5} with edges of weight 3, rungs
+    # 0-3 (5), 1-4 (6), 2-5 (5).  d = 11, 12, 11, 11, 12, 11; bound = delta
+    # = 11.  PR1 (c >= 11) and PR2 (2c > min d: triangle 6 > 11, rungs
+    # 10 > 11, 12 > 12, 10 > 11) pass nothing; every vertex has three arcs.
+    # PR3 for edge {u, v} with common neighbour w needs
+    # 2(c(u,v) + c(u,w)) > d(u) and 2(c(u,v) + c(v,w)) > d(v):
+    #   0-2 (w = 1): 12 > d0 = 11 and 12 > d2 = 11          passes
+    #   0-1 (w = 2): 12 > d0 = 11 but 12 > d1 = 12 is false  fails
+    #   1-2 (w = 0): 12 > d1 = 12 is false                   fails
+    # and the same in the second triangle (3-5 passes); rungs have no common
+    # neighbour.  PR4 (level 4): c + min over the common neighbour = 3 + 3
+    # = 6 < 11 on every triangle edge, so level 4 adds nothing.
+    # Blocks {0, 2}, {1}, {3, 5}, {4}: labels 0, 1, 0, 3, 4, 3.
+    u = np.array([0, 0, 1, 3, 3, 4, 0, 1, 2])
+    v = np.array([1, 2, 2, 4, 5, 5, 3, 4, 5])
+    c = np.array([3, 3, 3, 3, 3, 3, 5, 6, 5])
+    g = graphgen.from_edges(6, u, v, c)
+    assert list(oracle.degrees(*g)) == [11, 12, 11, 11, 12, 11]
+    assert list(oracle.pr_tests(*g, 11, 2)) == [0, 1, 2, 3, 4, 5]
+    for level in (3, 4):
+        lab = oracle.pr_tests(*g, 11, level)
+        assert list(lab) == [0, 1, 0, 3, 4, 3], level
+        assert _blocks_safe(g, lab, 11)
+
+
+def _parity(seed, sweep, v):
+    # the half-sweep a vertex updates in (label-propagation reading):
+    # the low bit of splitmix64(seed ^ splitmix64((sweep << 32) | v)), with
+    # splitmix64 pinned to its published output above
+    return oracle.splitmix64(seed ^ oracle.splitmix64((sweep << 32) | v)) & 1
+
+
+def _seed_with_parities(pattern):
+    for seed in range(1 << 16):
+        if [_parity(seed, 0, v) for v in range(len(pattern))] == pattern:
+            return seed
+    raise AssertionError("no seed with that parity pattern")
+
+
+def test_label_prop_half_sweeps_are_synchronous():
+    # Unit path 0 - 1 - 2 - 3 - 4, one sweep, every vertex in half-sweep 0.
+    # Each vertex takes its neighbours' heaviest label, ties to the smallest,
+    # from the labels as they stood before the half-sweep:
+    #   v0: {1} -> 1;  v1: {0, 2} tie -> 0;  v2: {1, 3} -> 1;
+    #   v3: {2, 4} -> 2;  v4: {3} -> 3;  half-sweep 1 moves no vertex.
+    # Result 1, 0, 1, 2, 3.  Updating in place in vertex order would give
+    # 1, 1, 1, 1, 1 instead (v1 would already see label 1 at v0, and so on).
+    g = graphgen.from_edges(5, np.array([0, 1, 2, 3]), np.array([1, 2, 3, 4]))
+    seed = _seed_with_parities([0, 0, 0, 0, 0])
+    assert list(oracle.label_prop(*g, iters=1, seed=seed)) == [1, 0, 1, 2, 3]
+
+
+def test_label_prop_parity_split():
+    # The same path with parities 0, 1, 0, 1, 0 in sweep 0.
+    # Half-sweep 0 (v0, v2, v4 at once, from 0, 1, 2, 3, 4):
+    #   v0 -> 1;  v2: {1, 3} -> 1;  v4 -> 3           labels 1, 1, 1, 3, 3
+    # Half-sweep 1 (v1, v3, from those labels):
+    #   v1: {0: 1, 2: 1} -> 1 (weight 2);  v3: {2: 1, 4: 3} tie -> 1
+    # Result 1, 1, 1, 1, 3.  Without the split (all vertices in both
+    # half-sweeps) it would be 0, 1, 0, 1, 2.
+    g = graphgen.from_edges(5, np.array([0, 1, 2, 3]), np.array([1, 2, 3, 4]))
+    seed = _seed_with_parities([0, 1, 0, 1, 0])
+    assert list(oracle.label_prop(*g, iters=1, seed=seed)) == [1, 1, 1, 1, 3]
+
+
+def test_label_prop_weighted_choice():
+    # A star centre 0 with leaves 1 (weight 1), 2 (weight 1), 3 (weight 2)
+    # and the edge 2 - 3 (weight 1); every vertex in half-sweep 0.
+    # v0: labels 1 (1), 2 (1), 3 (2) -> 3;  v1: {0} -> 0;
+    # v2: {0: 1, 3: 1} tie -> 0;  v3: {0: 2, 2: 1} -> 0.
+    # Result 3, 0, 0, 0: the heavier arc wins over the smaller label.
+    g = graphgen.from_edges(4, np.array([0, 0, 0, 2]), np.array([1, 2, 3, 3]),
+                            np.array([1, 1, 2, 1]))
+    seed = _seed_with_parities([0, 0, 0, 0])
+    assert list(oracle.label_prop(*g, iters=1, seed=seed)) == [3, 0, 0, 0]
 
 
 def test_planted_4096_two_exact_algorithms_agree():
