@@ -187,13 +187,14 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,
  *   bitmap_word_off  G+1 int64, required when bitmaps is non-NULL
  * One kernel launch solves the whole batch: one warp per graph, graphs
  * taken largest first (Alg. 2 per graph with full capped scans, PR1/PR2 and
- * in-warp contraction).  Inputs must be symmetric (not checked here);
- * self-loops and zero weights are dropped and parallel arcs merged; a
+ * in-warp contraction).  Self-loops and zero weights are dropped and
+ * parallel arcs merged; after that every graph must be symmetric (each arc
+ * (u, v, c) has its mirror (v, u, c)), which the kernel checks per graph; a
  * disconnected graph gets lambda 0.  stats: n_input/m_input are totals,
  * ms_total is the kernel's device time.
  * Errors: MC_EINVAL (n_g < 2, bad offsets, neighbour out of range, negative
- * weight), MC_EOVERFLOW, MC_ENOMEM, MC_ECUDA, MC_EINTERNAL -- the first
- * failing graph's code.
+ * weight, an arc without its mirror), MC_EOVERFLOW, MC_ENOMEM, MC_ECUDA,
+ * MC_EINTERNAL -- the first failing graph's code.
  */
 int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
                      const int32_t *row_ptr, const int32_t *col, const int32_t *w,
@@ -270,9 +271,18 @@ int mc_step_degrees(mc_graph *g, int64_t *deg);
 int mc_step_contract(mc_graph *g, const int32_t *lab, int32_t nc, int64_t clamp,
                      int32_t *row_ptr, int32_t *col, int32_t *w, int64_t *arcs_out);
 
-/* Padberg-Rinaldi tests 1..level against bound `lam` (reading stated in
- * DESIGN and in the kernel source); labels[v] = smallest vertex of v's
- * block in the graph of passing edges.                                    */
+/* Padberg-Rinaldi tests 1..level against bound `lam` (Sec. 2.2 and 2.3 cite
+ * them without stating them).  With d() the weighted degree, edge {u, v}
+ * passes
+ *   PR1: c(u,v) >= lam;
+ *   PR2: 2 c(u,v) > min(d(u), d(v));
+ *   PR3: a common neighbour w has 2(c(u,v) + c(u,w)) > d(u) and
+ *        2(c(u,v) + c(v,w)) > d(v);
+ *   PR4: c(u,v) + sum over common neighbours w of min(c(u,w), c(v,w)) >= lam;
+ * and from level 2 on, a vertex whose only two arcs have equal weight joins
+ * the smaller of its two neighbours.  PR2 and PR3 are strict because every
+ * passing edge is contracted at once.  labels[v] = smallest vertex of v's
+ * block in the graph of passing edges. */
 int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels);
 
 /* One round of concurrent capped CAPFOREST scans (Alg. 1) at bound `lam`:
@@ -289,8 +299,14 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt,
 int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *labels,
                            int64_t *lam_out, int64_t *unions_out);
 
-/* `iters` label-propagation sweeps (reading stated in DESIGN and in the
- * kernel source); labels n int32.                                         */
+/* `iters` label-propagation sweeps (VieCut's clustering, Sec. 2.3, which
+ * does not state the rule).  Labels start as the vertex ids; each sweep has
+ * two half-sweeps p = 0, 1, and in half-sweep p every vertex v with
+ * parity(seed, sweep, v) = p takes, all at once from the labels as they
+ * stood, the label of largest total arc weight among its neighbours (ties to
+ * the smaller label; a vertex without neighbours keeps its own), where
+ * parity(seed, s, v) = splitmix64(seed ^ splitmix64((s << 32) | v)) & 1.
+ * labels: n int32. */
 int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *labels);
 
 /* ---- allocation-free full scan -------------------------------------------
@@ -318,7 +334,12 @@ int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *label
  * its address (cudaGetSymbolAddress) -- make that call before any stream
  * capture.  Calls share the array: overlapping calls on one device race and
  * must be serialised by the caller.  Sizes beyond the limits below return
- * MC_EINVAL before any device work.
+ * MC_EINVAL before any device work.  The arrays are checked on the device
+ * before anything they index is touched: bad row offsets (row_ptr[0] != 0,
+ * a decrease, row_ptr[n] != arcs), a neighbour outside [0, n), a self-loop or
+ * a weight below 1 return MC_EINVAL.  Symmetry is not checked: an
+ * asymmetric graph gives meaningless labels, but every access stays inside
+ * the arrays.
  */
 #define MC_NOALLOC_MAX_N 32768
 #define MC_NOALLOC_MAX_ARCS 262144

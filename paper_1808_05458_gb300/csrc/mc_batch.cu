@@ -269,6 +269,60 @@ __device__ long long warp_contract(const int *in_src, const int2 *in_adj, long l
     return out;
 }
 
+// Stable transpose of the arcs (src[i] -> adj[i].x, weight adj[i].y), i in
+// [0, m), over n vertices: row v of the result lists (u, c) for every arc
+// u -> v in the input's index order; out_src[j] = v.  An input whose arcs
+// are ordered by source yields rows sorted by source.
+__device__ void warp_transpose(const int *src, const int2 *adj, long long m, int n, int *out_rp,
+                               int *out_src, int2 *out_adj, int *cnt, int *cursor) {
+    const int lane = lane_id();
+    for (int v = lane; v < n; v += 32) cnt[v] = 0;
+    __syncwarp();
+    for (long long i = lane; i < m; i += 32) atomicAdd(&cnt[adj[i].x], 1);
+    __syncwarp();
+    warp_excl_scan(cnt, out_rp, n);
+    for (int v = lane; v < n; v += 32) cursor[v] = out_rp[v];
+    __syncwarp();
+    for (long long i0 = 0; i0 < m; i0 += 32) {
+        const long long i = i0 + lane;
+        int v = -1 - lane, u = 0, c = 0;
+        if (i < m) {
+            v = adj[i].x;
+            c = adj[i].y;
+            u = src[i];
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, v);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int base = 0;
+        if (v >= 0) base = cursor[v];
+        __syncwarp();
+        if (v >= 0) {
+            out_adj[base + rank] = make_int2(u, c);
+            out_src[base + rank] = v;
+            if (rank == 0) cursor[v] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// Symmetry of a canonical CSR (every row free of duplicates, arcs ordered by
+// source): T1 = transpose(G) has rows sorted by source, T2 = transpose(T1) is
+// G with its rows sorted, and G is symmetric (every arc (u, v, c) has its
+// mirror (v, u, c)) exactly when T1 and T2 are equal entry for entry.
+__device__ bool warp_symmetric(const int *src, const int2 *adj, long long m, int n, int *rp1, int *src1,
+                               int2 *adj1, int *rp2, int *src2, int2 *adj2, int *cnt, int *cursor) {
+    const int lane = lane_id();
+    warp_transpose(src, adj, m, n, rp1, src1, adj1, cnt, cursor);
+    warp_transpose(src1, adj1, m, n, rp2, src2, adj2, cnt, cursor);
+    bool bad = false;
+    for (int v = lane; v <= n; v += 32) bad |= rp1[v] != rp2[v];
+    for (long long i = lane; i < m; i += 32) {
+        const int2 a = adj1[i], b = adj2[i];
+        bad |= a.x != b.x || a.y != b.y;
+    }
+    return !__any_sync(0xffffffffu, bad);
+}
+
 // flatten the union-find par[0..n) into root[] and number the blocks in
 // lab[] (order of the smallest member); returns the block count
 __device__ int warp_relabel(int *par, int *root, int *lab, int *cnt, int n) {
@@ -461,6 +515,11 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     long long arcs = warp_contract(S.srcB, S.adjB, m, S.lab, n0, kInt32Max, S.rpT, S.adjT, S.rpA,
                                    S.srcA, S.adjA, S.deg, S.cnt, S.mark, &ovf);
     if (__reduce_or_sync(0xffffffffu, ovf)) err = MC_EOVERFLOW;
+    // an arc without its mirror (same weight after merging) is malformed
+    // input: the raw-arc buffers (B) and the sort buffers (T) are free here
+    if (!err && !warp_symmetric(S.srcA, S.adjA, arcs, n0, S.rpT, S.srcB, S.adjB, S.rpB, S.eslot, S.adjT,
+                                S.cnt, S.mark))
+        err = MC_EINVAL;
 
     long long lam = 0;
     if (!err) {

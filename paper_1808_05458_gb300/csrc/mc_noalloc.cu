@@ -45,25 +45,13 @@ constexpr size_t kNaBytes = kNaNext + round_up(sizeof(int) * kNaPool);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// zero the per-vertex state, compute the weighted degrees (self-loops are
-// not cut edges and are skipped), and reset the status block
-__global__ void k_na_prepare(int n, const int *__restrict__ rp, const int2 *__restrict__ adj,
-                             long long lam) {
-    int *T = reinterpret_cast<int *>(g_noalloc_scratch + kNaT);
-    int *r = reinterpret_cast<int *>(g_noalloc_scratch + kNaR);
-    long long *deg = reinterpret_cast<long long *>(g_noalloc_scratch + kNaDeg);
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        long long d = 0;
-        for (int a = rp[v]; a < rp[v + 1]; ++a) {
-            const int2 e = adj[a];
-            if (e.x != v) d += e.y;
-        }
-        deg[v] = d;
-        T[v] = 0;
-        r[v] = 0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Status *st = reinterpret_cast<Status *>(g_noalloc_scratch + kNaStatus);
+// Input checks before any access that the input indexes: one block resets
+// the status block, then checks the row offsets (row_ptr[0] = 0,
+// non-decreasing, row_ptr[n] = arcs); a bad offset sets kErrRange.
+__global__ void __launch_bounds__(1024) k_na_check_rp(int n, long long arcs, const int *__restrict__ rp,
+                                                     long long lam) {
+    Status *st = reinterpret_cast<Status *>(g_noalloc_scratch + kNaStatus);
+    if (threadIdx.x == 0) {
         st->lam = lam;
         st->unions = 0;
         st->scanned_arcs = 0;
@@ -74,6 +62,48 @@ __global__ void k_na_prepare(int n, const int *__restrict__ rp, const int2 *__re
         st->scan_ids = 0;
         st->cursor = 0;
     }
+    __syncthreads();
+    bool bad = false;
+    for (int v = threadIdx.x; v <= n; v += blockDim.x) {
+        const int a = rp[v];
+        if (v == 0 && a != 0) bad = true;
+        if (v == n && (long long)a != arcs) bad = true;
+        if (v < n && rp[v + 1] < a) bad = true;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) st->err |= kErrRange;
+}
+
+// One warp per row, only once the offsets passed: checks every arc
+// (neighbour in [0, n), not the row's own vertex, weight >= 1), sums the
+// weighted degree and zeroes the row's scan state.  A bad arc sets kErrRange
+// and nothing downstream runs.
+__global__ void __launch_bounds__(256) k_na_prepare(int n, const int *__restrict__ rp,
+                                                    const int2 *__restrict__ adj) {
+    Status *st = reinterpret_cast<Status *>(g_noalloc_scratch + kNaStatus);
+    if (*(volatile int *)&st->err) return;
+    int *T = reinterpret_cast<int *>(g_noalloc_scratch + kNaT);
+    int *r = reinterpret_cast<int *>(g_noalloc_scratch + kNaR);
+    long long *deg = reinterpret_cast<long long *>(g_noalloc_scratch + kNaDeg);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    bool bad = false;
+    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
+        const int a0 = rp[v], a1 = rp[v + 1];
+        long long d = 0;
+        for (int a = a0 + lane; a < a1; a += 32) {
+            const int2 e = adj[a];
+            if (e.x < 0 || e.x >= n || e.x == v || e.y < 1) bad = true;
+            d += e.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) {
+            deg[v] = d;
+            T[v] = 0;
+            r[v] = 0;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->err, kErrRange);
 }
 
 std::mutex g_na_mutex;
@@ -124,10 +154,22 @@ extern "C" int mc_capforest_full_noalloc(int32_t n, int64_t arcs, const int32_t 
     g.adj = reinterpret_cast<int2 *>(const_cast<int32_t *>(adj));
     g.deg = reinterpret_cast<i64 *>(base + kNaDeg);
 
-    int blocks = (n + 255) / 256;
-    if (blocks > 1024) blocks = 1024;
-    ++::mc::g_launches; k_na_prepare<<<blocks, 256, 0, s>>>(n, row_ptr, g.adj, lam);
+    ++::mc::g_launches; k_na_check_rp<<<1, 1024, 0, s>>>(n, arcs, row_ptr, lam);
     MC_CUDA(cudaGetLastError());
+    int blocks = (n + 7) / 8;
+    if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
+    ++::mc::g_launches; k_na_prepare<<<blocks, 256, 0, s>>>(n, row_ptr, g.adj);
+    MC_CUDA(cudaGetLastError());
+    {
+        int err = 0;
+        MC_CUDA(cudaMemcpyAsync(&err, &st->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (err) {
+            set_error_detail("mc_capforest_full_noalloc: bad row offsets, or an arc with a neighbour "
+                             "out of range, a self-loop or a weight below 1");
+            return MC_EINVAL;
+        }
+    }
     int *par = reinterpret_cast<int *>(base + kNaPar);
     MC_TRY(iota_i32(par, n, s));
     MC_TRY(capforest_full_raw(g, par, reinterpret_cast<int *>(base + kNaT),

@@ -613,6 +613,29 @@ def test_batch_invalid(mc):
         mc.batch_min_cut(*b)
 
 
+def test_batch_asymmetric_rejected(mc):
+    # a graph whose arc lacks its mirror, or whose mirror has another weight,
+    # is malformed input: the whole call returns MC_EINVAL
+    rp, col, w = graphgen.cycle(7, 3)
+    good = graphgen.complete(5, 2)
+    w_bad = w.copy()
+    w_bad[0] += 1                      # (0, 1, 4) against (1, 0, 3)
+    rp_m = np.array([0, 1, 2, 2], dtype=np.int32)   # 0 -> 1 and 1 -> 2 without mirrors
+    col_m = np.array([1, 2], dtype=np.int32)
+    w_m = np.array([1, 1], dtype=np.int32)
+    for bad in ((rp, col, w_bad), (rp_m, col_m, w_m)):
+        for graphs in ([bad], [good, bad, good]):
+            with pytest.raises(mc.MinCutError) as ei:
+                mc.batch_min_cut(*_concat(graphs))
+            assert ei.value.code == mc.MC_EINVAL
+    # parallel arcs that merge into a symmetric graph are accepted: 0 -> 1
+    # given as 2 + 3 in row 0 and as 5 in row 1
+    rp_p = np.array([0, 2, 3], dtype=np.int32)
+    g_par = (rp_p, np.array([1, 1, 0], dtype=np.int32), np.array([2, 3, 5], dtype=np.int32))
+    lam, _, _, _ = mc.batch_min_cut(*_concat([good, g_par]))
+    assert list(lam) == [8, 5]
+
+
 def test_batch_4096_full(mc):
     # the batched workload: 4096 graphs, n in 50..2000, degree 4..16, weights 1..100
     b = graphgen.batch(1)

@@ -47,10 +47,20 @@ def test_noalloc_matches_allocating_scan_twice(which):
         for start in (0, n // 2):
             ref_lab, ref_lam, ref_un = G.capforest_full(lam, start)
             labels = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-            for _ in range(2):
-                lo, un = mincut.capforest_full_noalloc(d_rp, d_adj, lam, start, labels)
+            torch.cuda.synchronize()
+            before = torch.cuda.memory_allocated()
+            # the library's next device allocation would fail: the calls
+            # below must not make one
+            mc.test_fail_alloc_after(0)
+            try:
+                got = [mincut.capforest_full_noalloc(d_rp, d_adj, lam, start, labels)
+                       + (labels.cpu().numpy(),) for _ in range(2)]
+            finally:
+                mc.test_fail_alloc_after(-1)
+            assert torch.cuda.memory_allocated() == before
+            for lo, un, lab in got:
                 assert lo == ref_lam and un == ref_un
-                assert (labels.cpu().numpy() == ref_lab).all()
+                assert (lab == ref_lab).all()
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch():
@@ -72,3 +82,34 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
                                        ctypes.c_void_p(lab.data_ptr()), ctypes.byref(lo),
                                        ctypes.byref(un), None)
     assert rc == mincut.MC_EINVAL
+
+
+def test_noalloc_rejects_malformed_arrays():
+    # bad offsets or arcs are caught on the device before the scan indexes
+    # anything with them, and the next good call still works
+    import torch
+    from paper_1808_05458_gb300 import mincut
+
+    g = graphgen.cycle(12, 3)
+    rp = torch.from_numpy(g[0]).cuda()
+    adj = torch.from_numpy(np.stack([g[1], g[2]], axis=1).reshape(-1).astype(np.int32)).cuda()
+    lab = torch.zeros(12, dtype=torch.int32, device="cuda")
+    bad_cases = []
+    a = adj.clone(); a[6] = 12            # neighbour out of range
+    bad_cases.append((rp, a))
+    a = adj.clone(); a[6] = -1            # negative neighbour
+    bad_cases.append((rp, a))
+    a = adj.clone(); a[7] = 0             # weight below 1
+    bad_cases.append((rp, a))
+    a = adj.clone(); a[0] = 0             # self-loop in row 0
+    bad_cases.append((rp, a))
+    r = rp.clone(); r[5] = 30             # offsets not monotone
+    bad_cases.append((r, adj))
+    r = rp.clone(); r[0] = 1              # row_ptr[0] != 0
+    bad_cases.append((r, adj))
+    for d_rp, d_adj in bad_cases:
+        with pytest.raises(mincut.MinCutError) as ei:
+            mincut.capforest_full_noalloc(d_rp, d_adj, 6, 0, lab)
+        assert ei.value.code == mincut.MC_EINVAL
+    lo, un = mincut.capforest_full_noalloc(rp, adj, 6, 0, lab)
+    assert lo == 6 and un >= 1
