@@ -35,6 +35,7 @@ UNIT = "edges/s"
 # variant the paper reports at this point.
 PAPER_EDGES_PER_S = 1e9 / 32.91
 WORKLOAD = "rhg_n2^20_deg32_gamma5_lcc_unit"
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1808_05458_gb300", "weights", "proposer_rhg16_d64.bin")
 
 
 def dist_env():
@@ -190,6 +191,103 @@ def run_reference(args, rank, world):
     return 0
 
 
+def form_batched(mc, peak, seed=1):
+    """The batched form (4096 graphs, n in 50..2000, degree 4..16, weights
+    1..100): one mc_batch_min_cut per step through the C ABI from host
+    arrays (H2D of the batch, one persistent launch, D2H of the lambdas and
+    side bitmaps), every lambda checked against the oracle's lambdas stored
+    in tests/golden/batch_lambdas_seed1.json (written by the script beside
+    it), and the plain path (mc_graph_create + mc_min_cut per graph) timed on
+    every 16th graph of the same batch."""
+    import graphgen
+    b = graphgen.batch(seed)
+    G = len(b[3]) - 1
+    with open(os.path.join(ROOT, "tests", "golden", f"batch_lambdas_seed{seed}.json")) as f:
+        stored = json.load(f)
+    h = hashlib.sha256()
+    for a in b:
+        h.update(a.tobytes())
+    assert h.hexdigest()[:16] == stored["arrays_sha256_16"], "batch generator output changed"
+    ref = np.array(stored["lambdas"], dtype=np.int64)
+    mc.batch_autotune(*b)
+    for _ in range(2):
+        lam, _, _, st = mc.batch_min_cut(*b, bitmaps=True)
+    assert (lam == ref).all()
+    wall, dev = [], []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        lam, _, _, st = mc.batch_min_cut(*b, bitmaps=True)
+        wall.append(time.perf_counter() - t0)
+        dev.append(st["ms_total"] / 1e3)
+        assert (lam == ref).all()
+    sample = range(0, G, 16)
+    p_wall = p_dev = 0.0
+    for k in sample:
+        g = graphgen.batch_graph(b, k)
+        t0 = time.perf_counter()
+        with mc.Graph(*g) as gr:
+            r = gr.min_cut()
+        p_wall += time.perf_counter() - t0
+        p_dev += r.stats["ms_total"] / 1e3
+        assert r.lam == ref[k]
+    scale = G / len(sample)
+    vo, ao = b[3], b[4]
+    n_tot, a_tot = int(vo[-1]), int(ao[-1])
+    # algorithmic bytes of one batched solve, counted as the least the method
+    # moves: the input CSR read once (4 B per row offset, 8 B per arc), one
+    # full capped scan (8 B per arc, 24 B per vertex) and one contraction
+    # (12 B read, 16 B written per arc)
+    alg = 4 * (n_tot + G) + 8 * a_tot + (8 * a_tot + 24 * n_tot) + 28 * a_tot
+    kern = min(dev)
+    return {
+        "workload": "batch_4096_n50-2000_deg4-16_w1-100",
+        "graphs": G, "vertices": n_tot, "edges": a_tot // 2,
+        "solves_per_s": G / kern, "ms_kernel": kern * 1e3,
+        "e2e_solves_per_s": G / min(wall), "ms_e2e": min(wall) * 1e3,
+        "h2d_bytes_per_step": int(4 * (len(b[0]) + len(b[1]) + len(b[2])) + 16 * (G + 1)),
+        "plain_solves_per_s": G / (p_dev * scale), "plain_e2e_solves_per_s": G / (p_wall * scale),
+        "plain_sample": f"every 16th graph ({len(sample)} graphs), scaled to {G}",
+        "vs_plain": p_dev * scale / kern, "vs_plain_e2e": p_wall * scale / min(wall),
+        "lambda_checked": f"all {G} equal to the oracle's stored NOI results",
+        "roofline": {"bound": "hbm", "achieved": alg / kern / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / kern / 1e9 / peak, "traffic": None,
+                     "note": "one warp per graph; latency-bound (dependent per-pop loads)"},
+    }
+
+
+def form_bounds(mc, peak, name, g, proposer):
+    """Solve times of one resident graph with each initial bound: minimum
+    degree (the plain path), label propagation (VieCut), the learned
+    proposer, and the best of both; lambda must not change."""
+    import torch
+    n, m = len(g[0]) - 1, len(g[1]) // 2
+    out = {"workload": name, "n": n, "m": m}
+    stream = torch.cuda.current_stream()
+    with mc.Graph(*g) as G:
+        lam = None
+        for label, b in (("degree", mc.MC_BOUND_DEGREE), ("lp", mc.MC_BOUND_LP),
+                         ("learned", mc.MC_BOUND_LEARNED), ("best", mc.MC_BOUND_BEST)):
+            o = mc.options(bound=b, proposer=proposer.handle, cuda_stream=stream.cuda_stream)
+            G.min_cut(o)
+            ms, r = [], None
+            for _ in range(3):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = G.min_cut(o)
+                e.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(e))
+            lam = r.lam if lam is None else lam
+            assert r.lam == lam, (label, r.lam, lam)
+            t = min(ms)
+            out[label] = {"ms": t, "edges_per_s": m / (t / 1e3), "bound": r.stats["bound_initial"],
+                          "rounds": r.stats["rounds"], "ms_bound": r.stats["ms_bound"],
+                          "hbm_frac_whole_solve": r.stats["bytes_alg"] / (t / 1e3) / 1e9 / peak}
+        out["lambda"] = lam
+        out["delta"] = int(G.degrees().min())
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_1808_05458_gb300 as mc
@@ -315,6 +413,19 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
     }
     G.close()
+    del flush
+    if rank == 0 and world == 1 and not args.no_forms:
+        # the metric's chosen forms beside the plain path
+        import graphgen
+        forms = {"batched": form_batched(mc, peak, args.seed)}
+        P = mc.Proposer.load(LEARNED_WEIGHTS)
+        forms["bounds"] = [
+            form_bounds(mc, peak, "rhg_n2^23_deg64_gamma5_lcc_unit",
+                        graphgen.rhg(args.seed, 1 << 23, 64.0), P),
+            form_bounds(mc, peak, "planted_rhg_2x2^20_deg64_gamma5_cross8_unit",
+                        graphgen.planted_rhg(args.seed, 1 << 20, 64.0, cross=8), P)]
+        P.close()
+        line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -330,6 +441,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and bound-form measurements")
     ap.add_argument("--rhg-log2", type=int, default=20,
                     help="log2 of the RHG point count (20 = the benchmark workload; smaller "
                          "sizes are for profiling captures)")

@@ -103,6 +103,36 @@ def rmat_kcore(seed: int, scale: int = 22, edge_factor: int = 16, a: float = 0.5
     return _take(_load().gg_rmat_kcore(seed, scale, edge_factor, a, b, c, k, wmax))
 
 
+def planted_rhg(seed: int, n_block: int = 1 << 19, avg_deg: float = 32.0, gamma: float = 5.0,
+                cross: int = 3):
+    """Two threshold RHG graphs (largest components, seeds 2*seed+1 and
+    2*seed+2) joined by `cross` distinct random unit edges: a workload of the
+    paper's RHG family whose minimum cut (at most `cross`) lies below the
+    minimum degree and splits the graph into two large sides.  Vertices of
+    the first graph come first; unit weights."""
+    ra, ca, _ = rhg(2 * seed + 1, n_block, avg_deg, gamma)
+    rb, cb, _ = rhg(2 * seed + 2, n_block, avg_deg, gamma)
+    na, nb = len(ra) - 1, len(rb) - 1
+    rng = np.random.default_rng([seed, 0x9EC7])
+    pairs = set()
+    while len(pairs) < cross:
+        pairs.add((int(rng.integers(0, na)), int(na + rng.integers(0, nb))))
+    cu = np.array(sorted(pairs), dtype=np.int64).reshape(-1, 2)
+    cv = cu[np.lexsort((cu[:, 0], cu[:, 1]))]   # the same edges ordered by (v, u)
+    src = np.concatenate([np.repeat(np.arange(na), np.diff(ra)), cu[:, 0], cv[:, 1],
+                          na + np.repeat(np.arange(nb), np.diff(rb))])
+    dst = np.concatenate([ca.astype(np.int64), cu[:, 1], cv[:, 0], na + cb.astype(np.int64)])
+    # a stable sort by source keeps each row sorted: in a row of the first
+    # graph the cross arcs (to ids >= na) follow its own arcs, in a row of the
+    # second they (to ids < na) come first
+    order = np.argsort(src, kind="stable")
+    n = na + nb
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, src + 1, 1)
+    col = dst[order].astype(np.int32)
+    return np.cumsum(rp).astype(np.int32), col, np.ones(len(col), dtype=np.int32)
+
+
 def batch(seed: int, G: int = 4096, nmin: int = 50, nmax: int = 2000, dmin: int = 4,
           dmax: int = 16, wmax: int = 100):
     """G connected weighted graphs: returns (row_ptr, col, w, vtx_off, arc_off)

@@ -87,3 +87,22 @@ def test_seeded_and_pure(make):
     a, b, c = make(5), make(5), make(6)
     assert all((x == y).all() for x, y in zip(a, b))
     assert any(len(x) != len(y) or (x != y).any() for x, y in zip(a, c))
+
+
+def test_batch_lambdas_golden_file():
+    # the stored lambdas of the batched workload belong to these very graphs
+    # and agree with the oracle on a sample (the benchmark checks every
+    # batched result against the file)
+    import json
+    import os
+    import sys
+    import oracle
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    from make_batch_lambdas import batch_digest
+    d = json.load(open(os.path.join(here, "batch_lambdas_seed1.json")))
+    b = graphgen.batch(1)
+    assert d["arrays_sha256_16"] == batch_digest(b)
+    assert len(d["lambdas"]) == len(b[3]) - 1
+    for k in range(0, len(b[3]) - 1, 97):
+        assert d["lambdas"][k] == oracle.noi(*graphgen.batch_graph(b, k))[0]
