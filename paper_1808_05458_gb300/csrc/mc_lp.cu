@@ -9,20 +9,31 @@
 // the smallest label; a vertex without neighbours keeps its label), where
 //   parity(seed, s, v) = splitmix64(seed ^ splitmix64((s << 32) | v)) & 1.
 //
-// Kernels: one warp per vertex.  Rows of <= 32 arcs sum equal labels across
-// the warp's registers; rows of <= kLpSmemRow arcs aggregate in a
-// per-warp shared-memory hash; longer rows are left to a block-per-vertex
-// kernel that aggregates in a global-memory hash slice of 2^k > deg slots.
+// Kernels: a warp takes 32 consecutive vertices at a time.  The rows of its
+// active vertices (at most kLpRow arcs each) are laid end to end and cut
+// into batches of whole rows holding at most kLpBatch arcs; every lane then
+// gathers up to kLpBatch / 32 arcs of a batch at once -- all of their
+// {neighbour, weight} loads issued together, then all of their label loads
+// -- and adds each arc's weight into a per-warp shared-memory hash keyed by
+// (row, label).  Each row's choice comes from two passes over the table: the
+// largest total weight (32-bit shared atomics while every total fits in 31
+// bits, else one lane compares them all), then the smallest label reaching
+// it.  Longer rows
+// go to a block-per-vertex kernel with a global-memory hash slice of
+// 2^k > deg slots.
 #include "mc_internal.cuh"
 
 namespace mc {
 
 namespace {
 
-constexpr int kLpWarps = 4;         // warps per block
-constexpr int kLpHash = 1024;       // per-warp hash slots
-constexpr int kLpSmemRow = 512;     // longest row handled by the warp kernel
+constexpr int kLpWarps = 4;         // warps per block (35 KB of shared memory)
+constexpr int kLpRow = 256;         // longest row handled by the warp kernel
+constexpr int kLpBatch = 256;       // arcs per batch (whole rows)
+constexpr int kLpPer = kLpBatch / 32;
+constexpr int kLpHash = 512;        // per-warp hash slots (load <= 1/2)
 constexpr int kLpBigThreads = 256;
+constexpr unsigned long long kLpEmpty = ~0ULL;
 
 __device__ __forceinline__ int lp_parity(u64 seed, int sweep, int v) {
     return (int)(splitmix64(seed ^ splitmix64(((u64)(unsigned)sweep << 32) | (u64)(unsigned)v)) & 1ULL);
@@ -43,118 +54,176 @@ __device__ __forceinline__ void warp_argmax(long long &w, int &l) {
 }
 
 struct LpSmem {
-    int key[kLpHash];
-    unsigned long long val[kLpHash];
-    unsigned long long sum[32];  // per-lane label weights of a short row
-    short used[kLpSmemRow];      // hash slots a longer row filled
-    int nused;
+    unsigned long long key[kLpHash];  // (row << 32) | label, or kLpEmpty
+    unsigned long long val[kLpHash];  // summed arc weight
+    unsigned bw[32];                  // per row: largest total weight (31-bit totals)
+    long long wide_w[32];             // per row: the same, when a total needs more bits
+    int bl[32];                       // per row: smallest label with it
+    int end[32];                      // per row: end of its arcs, laid end to end
+    int a0[32];                       // per row: its first arc
 };
 
-// Each warp takes 32 consecutive vertices at a time: their parities and row
-// bounds come in one coalesced step, vertices outside this half-sweep keep
-// their label, and the warp then works through the active ones.  A row of
-// <= 32 arcs groups equal labels with match_any and adds each group's
-// weights in shared memory at its lowest lane.
+__device__ __forceinline__ unsigned lp_slot(unsigned long long key) {
+    const unsigned x = (unsigned)key * 2654435761u ^ (unsigned)(key >> 32) * 0x85EBCA6Bu;
+    return x >> (32 - 9);
+}
+
 __global__ void __launch_bounds__(kLpWarps * 32)
 k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const int *__restrict__ lin,
           int *__restrict__ lout, u64 seed, int sweep, int half, int *big_list, int *big_count) {
+    static_assert(kLpHash == 512, "lp_slot takes 9 bits");
     __shared__ LpSmem sm[kLpWarps];
     LpSmem &h = sm[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < kLpHash; i += 32) { h.key[i] = -1; h.val[i] = 0; }
-    h.sum[lane] = 0;
-    if (lane == 0) h.nused = 0;
+    for (int i = lane; i < kLpHash; i += 32) { h.key[i] = kLpEmpty; h.val[i] = 0; }
+    h.bw[lane] = 0;
+    h.wide_w[lane] = -1;
+    h.bl[lane] = INT_MAX;
     __syncwarp();
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
         const int v = base + lane;
-        int a0 = 0, a1 = 0, cur = 0;
-        bool act = false;
+        int a0 = 0, d = 0;
         if (v < n) {
-            cur = lin[v];
+            const int cur = lin[v];
             a0 = rp[v];
-            a1 = rp[v + 1];
-            act = lp_parity(seed, sweep, v) == half && a1 > a0;
-            if (act && a1 - a0 > kLpSmemRow) {  // hub: the block kernel decides
+            d = rp[v + 1] - a0;
+            const bool act = lp_parity(seed, sweep, v) == half && d > 0;
+            if (act && d > kLpRow) {  // hub: the block kernel decides
                 big_list[atomicAdd(big_count, 1)] = v;
-                act = false;
+                d = 0;
             } else if (!act) {
                 lout[v] = cur;
+                d = 0;
             }
         }
-        unsigned todo = __ballot_sync(0xffffffffu, act);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int u = base + l;
-            const int r0 = __shfl_sync(0xffffffffu, a0, l), r1 = __shfl_sync(0xffffffffu, a1, l);
-            const int d = r1 - r0;
-            long long bw = -1;
-            int bl = INT_MAX;
-            if (d <= 32) {
-                int lab = -1 - lane;
-                int wt = 0;
-                if (lane < d) {
-                    const int2 e = adj[r0 + lane];
-                    lab = lin[e.x];
-                    wt = e.y;
-                }
-                const unsigned peers = __match_any_sync(0xffffffffu, lab);
-                const int lead = __ffs(peers) - 1;
-                if (lane < d) atomicAdd(&h.sum[lead], (unsigned long long)wt);
-                __syncwarp();
-                if (lane < d && lead == lane) { bw = (long long)h.sum[lane]; bl = lab; }
-                __syncwarp();
-                h.sum[lane] = 0;
-            } else {
-                for (int i = r0 + lane; i < r1; i += 32) {
-                    const int2 e = adj[i];
-                    const int lab = lin[e.x];
-                    unsigned hh = ((unsigned)lab * 2654435761u) >> (32 - 10);
-                    while (true) {
-                        const int k = atomicCAS(&h.key[hh], -1, lab);
-                        if (k == -1) { h.used[atomicAdd(&h.nused, 1)] = (short)hh; break; }
-                        if (k == lab) break;
-                        hh = (hh + 1) & (kLpHash - 1);
+        if (!__any_sync(0xffffffffu, d > 0)) continue;
+        // lay the active rows end to end (inclusive scan of their lengths)
+        int e = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, e, o);
+            if (lane >= o) e += t;
+        }
+        h.end[lane] = e;
+        h.a0[lane] = a0;
+        // greedy batches of whole rows with at most kLpBatch arcs each
+        int batch = 0, acc = 0, my_batch = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int dj = __shfl_sync(0xffffffffu, d, j);
+            if (acc + dj > kLpBatch) { ++batch; acc = 0; }
+            acc += dj;
+            if (lane == j) my_batch = batch;
+        }
+        __syncwarp();
+        for (int b = 0; b <= batch; ++b) {
+            const unsigned in_b = __ballot_sync(0xffffffffu, d > 0 && my_batch == b);
+            if (!in_b) continue;
+            const int jlo = __ffs(in_b) - 1, jhi = 31 - __clz(in_b);
+            const int p0 = jlo > 0 ? h.end[jlo - 1] : 0, p1 = h.end[jhi];
+            // this lane's arcs: positions p0 + lane + 32 k of the laid-out rows
+            int row[kLpPer], ai[kLpPer];
+#pragma unroll
+            for (int k = 0; k < kLpPer; ++k) {
+                const int p = p0 + lane + 32 * k;
+                row[k] = -1;
+                ai[k] = 0;
+                if (p < p1) {
+                    int lo = jlo, hi = jhi;  // the first row whose end lies past p
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (h.end[mid] > p) hi = mid; else lo = mid + 1;
                     }
-                    atomicAdd(&h.val[hh], (unsigned long long)e.y);
+                    row[k] = lo;
+                    ai[k] = h.a0[lo] + p - (lo > 0 ? h.end[lo - 1] : 0);
                 }
-                __syncwarp();
-                // the row's labels sit in the slots it filled (<= d of them);
-                // read them, then clear exactly those
-                const int nu = h.nused;
-                for (int i = lane; i < nu; i += 32) {
-                    const int slot = h.used[i];
-                    const int k = h.key[slot];
-                    if (lp_better((long long)h.val[slot], k, bw, bl)) { bw = (long long)h.val[slot]; bl = k; }
-                }
-                __syncwarp();
-                for (int i = lane; i < nu; i += 32) {
-                    const int slot = h.used[i];
-                    h.key[slot] = -1;
-                    h.val[slot] = 0;
-                }
-                if (lane == 0) h.nused = 0;
-                __syncwarp();
             }
-            warp_argmax(bw, bl);
-            if (lane == 0) lout[u] = bl;
+            int2 ed[kLpPer];
+#pragma unroll
+            for (int k = 0; k < kLpPer; ++k) ed[k] = row[k] >= 0 ? adj[ai[k]] : make_int2(0, 0);
+            int lab[kLpPer];
+#pragma unroll
+            for (int k = 0; k < kLpPer; ++k) lab[k] = row[k] >= 0 ? lin[ed[k].x] : 0;
+#pragma unroll
+            for (int k = 0; k < kLpPer; ++k) {
+                if (row[k] < 0) continue;
+                const unsigned long long key = ((unsigned long long)row[k] << 32) | (unsigned)lab[k];
+                unsigned sl = lp_slot(key);
+                while (true) {
+                    const unsigned long long old = atomicCAS(&h.key[sl], kLpEmpty, key);
+                    if (old == kLpEmpty || old == key) break;
+                    sl = (sl + 1) & (kLpHash - 1);
+                }
+                atomicAdd(&h.val[sl], (unsigned long long)ed[k].y);
+            }
+            __syncwarp();
+            // pass 1: each row's largest total weight, by 32-bit atomics while
+            // every total fits in 31 bits (else one lane compares them all)
+            bool wide = false;
+            for (int i = lane; i < kLpHash; i += 32) {
+                const unsigned long long key = h.key[i];
+                if (key == kLpEmpty) continue;
+                const unsigned long long t = h.val[i];
+                if (t >> 31) wide = true;
+                else atomicMax(&h.bw[key >> 32], (unsigned)t);
+            }
+            if (__any_sync(0xffffffffu, wide)) {
+                __syncwarp();
+                if (lane == 0) {
+                    for (int i = 0; i < kLpHash; ++i) {
+                        const unsigned long long key = h.key[i];
+                        if (key == kLpEmpty) continue;
+                        const int r = (int)(key >> 32);
+                        const int l = (int)(unsigned)key;
+                        if (lp_better((long long)h.val[i], l, h.wide_w[r], h.bl[r])) {
+                            h.wide_w[r] = (long long)h.val[i];
+                            h.bl[r] = l;
+                        }
+                        h.key[i] = kLpEmpty;
+                        h.val[i] = 0;
+                    }
+                }
+            } else {
+                __syncwarp();
+                // pass 2: the smallest label reaching it; empty the table
+                for (int i = lane; i < kLpHash; i += 32) {
+                    const unsigned long long key = h.key[i];
+                    if (key != kLpEmpty) {
+                        const int r = (int)(key >> 32);
+                        if (h.val[i] == (unsigned long long)h.bw[r]) atomicMin(&h.bl[r], (int)(unsigned)key);
+                        h.key[i] = kLpEmpty;
+                        h.val[i] = 0;
+                    }
+                }
+            }
+            __syncwarp();
+            if ((in_b >> lane) & 1u) {
+                lout[v] = h.bl[lane];
+                h.bw[lane] = 0;
+                h.wide_w[lane] = -1;
+                h.bl[lane] = INT_MAX;
+            }
+            __syncwarp();
         }
     }
 }
 
-// one block per hub vertex; hash slice of `cap` slots at hash_key/hash_val
+// one block per hub vertex; a hash slice of 2^cap_log2 slots per block at
+// hash_key/hash_val, of which a row of d arcs uses the smallest power of two
+// >= 2d (load at most 1/2)
 __global__ void __launch_bounds__(kLpBigThreads)
 k_lp_big(const int *__restrict__ rp, const int2 *__restrict__ adj, const int *__restrict__ lin,
          int *__restrict__ lout, const int *__restrict__ big_list, const int *big_count,
          int *hash_key, unsigned long long *hash_val, int cap_log2) {
-    const int cap = 1 << cap_log2;
     __shared__ long long sw[kLpBigThreads / 32];
     __shared__ int sl[kLpBigThreads / 32];
     for (int b = blockIdx.x; b < *big_count; b += gridDim.x) {
         const int v = big_list[b];
-        int *hk = hash_key + (size_t)blockIdx.x * cap;
-        unsigned long long *hv = hash_val + (size_t)blockIdx.x * cap;
+        int *hk = hash_key + ((size_t)blockIdx.x << cap_log2);
+        unsigned long long *hv = hash_val + ((size_t)blockIdx.x << cap_log2);
+        const int d = rp[v + 1] - rp[v];
+        int cap = 2;
+        while (cap < 2 * d && cap < (1 << cap_log2)) cap <<= 1;
         for (int i = threadIdx.x; i < cap; i += blockDim.x) { hk[i] = -1; hv[i] = 0; }
         __syncthreads();
         for (int i = rp[v] + threadIdx.x; i < rp[v + 1]; i += blockDim.x) {
@@ -212,20 +281,23 @@ int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cud
     ++::mc::g_launches; k_max_row<<<blocks_v, 256, 0, s>>>(g.rp, n, d_max);
     MC_TRY(status_read(w, s));
     const int maxrow = (int)w.h_st->count2;
-    // hub hash slices: 2^k > longest row slots each (an empty slot always
-    // ends a probe), as many slices as fit in one radix buffer (u64 weights
-    // in the key buffer, int keys in the value buffer)
+    // hub hash slices: 2^k >= twice the longest row slots each (an empty
+    // slot always ends a probe), as many slices as fit in one radix buffer
+    // (u64 weights in the key buffer, int keys in the value buffer)
     int cap_log2 = 1;
-    while ((1 << cap_log2) <= maxrow) ++cap_log2;
-    const bool hubs = maxrow > kLpSmemRow;
+    while ((1 << cap_log2) < 2 * maxrow) ++cap_log2;
+    // a row holding most of the graph's arcs: slices of 2^k > maxrow slots
+    // (still an empty slot in every probe)
+    if (((size_t)w.cap_arcs >> cap_log2) < 1 && (1 << (cap_log2 - 1)) > maxrow) --cap_log2;
+    const bool hubs = maxrow > kLpRow;
     size_t hub_blocks = (size_t)w.cap_arcs >> cap_log2;
-    if (hub_blocks > 256) hub_blocks = 256;
+    if (hub_blocks > (size_t)num_sms() * 8) hub_blocks = (size_t)num_sms() * 8;
     if (hubs && hub_blocks < 1) {
         set_error_detail("label propagation: hub rows too long for the hash workspace");
         return MC_ENOMEM;
     }
     int *cur = labels, *nxt = w.cnt;
-    int grid = num_sms() * 8;
+    int grid = num_sms() * 6;
     for (int it = 0; it < iters; ++it) {
         for (int half = 0; half < 2; ++half) {
             MC_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));

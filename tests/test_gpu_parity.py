@@ -739,7 +739,14 @@ def test_label_prop_parity(mc, iters):
     graphs = [graphgen.random_connected(500, 3000, seed=11, wmax=7),
               graphgen.planted(4, block_n=400, avg_deg=16, cross=6),
               graphgen.rhg(2, 1 << 14, 24.0),
-              graphgen.rmat_kcore(2, scale=14, k=6)]
+              graphgen.rmat_kcore(2, scale=14, k=6),
+              # rows of about 200-300 arcs on both sides of the warp kernel's
+              # row limit, every label distinct in the first half-sweep
+              graphgen.random_gnp(700, 0.36, seed=12, wmax=50),
+              # many rows of 1-3 arcs packed into one batch
+              graphgen.random_connected(5000, 1500, seed=13, wmax=4),
+              # weights near 2^30: a label's total in a row passes 2^31
+              graphgen.random_gnp(300, 0.1, seed=14, wmax=1 << 30)]
     # a star with a 3000-arc hub plus a ring, weights 1..9
     rng = np.random.default_rng(5)
     hub_u = np.zeros(3000, dtype=np.int64)
@@ -749,6 +756,9 @@ def test_label_prop_parity(mc, iters):
     u = np.concatenate([hub_u, ring_u])
     v = np.concatenate([hub_v, ring_v])
     graphs.append(graphgen.from_edges(3001, u, v, rng.integers(1, 10, size=len(u))))
+    # a pure star: one row holds half of all arcs
+    graphs.append(graphgen.from_edges(2001, np.zeros(2000, dtype=np.int64), np.arange(1, 2001),
+                                      rng.integers(1, 10, size=2000)))
     for k, g in enumerate(graphs):
         with mc.Graph(*g) as G:
             lab = G.label_prop(iters, seed=77 + k)
