@@ -35,7 +35,7 @@ UNIT = "edges/s"
 # variant the paper reports at this point.
 PAPER_EDGES_PER_S = 1e9 / 32.91
 WORKLOAD = "rhg_n2^20_deg32_gamma5_lcc_unit"
-LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1808_05458_gb300", "weights", "proposer_rhg16_d64.bin")
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1808_05458_gb300", "weights", "proposer_prhg16_d64.bin")
 
 
 def dist_env():

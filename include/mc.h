@@ -63,8 +63,10 @@ extern "C" {
 
 #define MC_BOUND_DEGREE 0  /* lambda-hat = minimum weighted degree            */
 #define MC_BOUND_LP 1      /* + label-propagation clustering bound (VieCut)   */
-#define MC_BOUND_LEARNED 2 /* + the learned proposer's sweep cut (opt.proposer) */
-#define MC_BOUND_BEST 3    /* + both                                          */
+#define MC_BOUND_LEARNED 2 /* + the learned proposer's sweep cut over one level
+                              of label-propagation clusters (opt.proposer)   */
+#define MC_BOUND_BEST 3    /* + both (the proposer on the LP bound's first
+                              level of clusters)                             */
 
 typedef struct mc_options {
     int32_t pq_order;        /* MC_PQ_LIFO (default) or MC_PQ_FIFO             */
@@ -227,14 +229,17 @@ const char *mc_strerror(int code);
 int mc_test_fail_alloc_after(int64_t k);
 
 /* ---- learned bound proposer -----------------------------------------------
- * A 3-layer message-passing network (hidden 64, BF16 activations, FP32
- * sums, tensor-core dense transforms) scores every vertex; the best sweep
- * cut over the scores is an exact integer cut of G and therefore an upper
- * bound on lambda.  mc_min_cut uses it only if it is below the bound it
- * already has, so lambda never depends on the network.  The paper has no
- * learned component.  Parameters are MC_PROPOSER_PARAMS floats (layout in
- * mc_learn.cu).  Graph arguments are graphs made by mc_graph_create; host
- * arrays unless stated.                                                     */
+ * A 3-layer message-passing network (hidden 64, BF16 weights and
+ * activations, FP32 sums, tensor-core dense transforms) scores every vertex
+ * of a graph; the best sweep cut over the scores is an exact integer cut and
+ * therefore an upper bound on lambda.  Its inputs are local degree features
+ * and two seeded random vectors smoothed by 32 steps of the lazy random walk
+ * (the sides of a sparse cut drift apart).  mc_min_cut runs it on one level
+ * of label-propagation clusters of G (MC_BOUND_LEARNED, MC_BOUND_BEST) and
+ * uses its cut only if it is below the bound it already has, so lambda never
+ * depends on the network.  The paper has no learned component.  Parameters
+ * are MC_PROPOSER_PARAMS floats (layout in mc_learn.cu).  Graph arguments are
+ * graphs made by mc_graph_create; host arrays unless stated.                */
 #define MC_PROPOSER_PARAMS 25409
 typedef struct mc_proposer mc_proposer;
 /* params: NULL = Glorot-uniform init from `seed` (biases 0). */
@@ -252,6 +257,14 @@ int mc_proposer_train_step(mc_proposer *p, mc_graph *g, const uint32_t *side, fl
 /* the best sweep cut over the scores: *cut (exact) and its side (bitmap,
  * canonical polarity, may be NULL) */
 int mc_proposer_bound(mc_proposer *p, mc_graph *g, int64_t *cut, uint32_t *side);
+/* The graph the proposer runs on inside mc_min_cut: `lp_iters` sweeps of
+ * label propagation (seed as in mc_step_label_prop) on g, the clusters
+ * contracted (Sec. 2.1) with merged weights clamped to g's minimum degree,
+ * returned as a new graph *out (caller destroys it); cluster_of (n int32,
+ * may be NULL) receives each vertex's cluster.  mc_min_cut uses seed
+ * (opt.seed ^ 0x9E37) and lp_iters (opt.lp_iters, 0 = 2).  MC_EINVAL when
+ * fewer than two clusters form.                                            */
+int mc_graph_coarsen(mc_graph *g, int32_t lp_iters, uint64_t seed, mc_graph **out, int32_t *cluster_of);
 
 /* ---- step-level entry points (same kernels as mc_min_cut) ---------------
  * These expose single steps of the path on a created graph for parity

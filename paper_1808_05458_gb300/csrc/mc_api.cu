@@ -216,9 +216,47 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
 // lambda-hat = min(., delta) -> PR tests -> contract }, then the exact loop on
 // what is left (at most kLpSmall vertices or no further clustering).  Runs on
 // Ga / Gb, leaves G0 untouched.
+// level 0 of the bound phase: `iters` label-propagation sweeps on G0, dense
+// cluster ids in w.lab, the cluster graph in Ga (merged weights clamped to
+// `clamp`), w.orig = each original vertex's cluster, the cluster graph's
+// minimum degree in w.h_st; *nc = clusters (the graph is left alone when
+// there are fewer than two)
+int cluster_level0(mc_graph *g, int iters, u64 seed, i64 clamp, int *nc, cudaStream_t s) {
+    Work &w = g->w;
+    MC_TRY(label_prop(g->G0, w, iters, seed, w.lab, s));
+    MC_TRY(compact_labels(w, g->n0, nc, s));
+    if (*nc < 2) return MC_OK;
+    MC_TRY(iota_i32(w.orig, g->n0, s));
+    MC_TRY(round_reset(w, clamp, s));
+    return contract_graph(g->G0, g->Ga, w, clamp, false, *nc, s, [&]() -> int {
+        MC_TRY(orig_update(w, g->n0, s));
+        return min_degree(g->Ga, w, s);
+    });
+}
+
+// the learned proposer's sweep cut over the clusters of `cl` (a cluster graph
+// whose vertices w.orig maps the original ones to): lowers lam, with its
+// side, when the cut is below it.  A sweep cut below the contraction's clamp
+// holds no clamped edge, so its weight is that of a real cut of G.
+int proposer_on_clusters(mc_graph *g, Proposer &pp, const DevGraph &cl, i64 delta_cl, i64 &lam, bool verbose,
+                         cudaStream_t s) {
+    long long cut = 0;
+    int k = 0;
+    MC_TRY(proposer_forward(pp, cl, delta_cl, s));
+    MC_TRY(proposer_sweep(pp, cl, g->w, &cut, &k, s));
+    if (verbose)
+        fprintf(stderr, "[mc] proposer on %d clusters: sweep cut %lld (k=%d), bound %lld\n", cl.n, cut, k,
+                (long long)lam);
+    if (cut < lam) {
+        lam = cut;
+        MC_TRY(side_from_rank(g->w, g->n0, k, true, s));
+    }
+    return MC_OK;
+}
+
 template <class Exact>
 int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool verbose, i64 &bytes,
-             Exact exact) {
+             Exact exact, Proposer *pp = nullptr) {
     Work &w = g->w;
     const int n0 = g->n0;
     constexpr int kLpSmall = 2048;
@@ -240,12 +278,15 @@ int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool ve
             return min_degree(*nxt, w, s);
         }));
         bytes += cur.arcs * 20;
-        if (w.h_st->mindeg < lam) {
-            lam = w.h_st->mindeg;
+        const i64 delta_cl = w.h_st->mindeg;
+        if (delta_cl < lam) {
+            lam = delta_cl;
             MC_TRY(side_from_vertex(w, n0, w.h_st->argmin, s));
         }
         cur = *nxt;
         nxt = (nxt == &g->Ga) ? &g->Gb : &g->Ga;
+        // the learned proposer votes on the first level's clusters
+        if (pp && level == 0) MC_TRY(proposer_on_clusters(g, *pp, cur, delta_cl, lam, verbose, s));
         // Padberg-Rinaldi on the cluster graph
         MC_TRY(union_find_init(w.par, cur.n, s));
         MC_TRY(round_reset(w, lam, s));
@@ -490,22 +531,21 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     // the label-propagation bound (VieCut, Sec. 2.3 / 3.1.1) on a contracted
     // copy: every candidate is the weight of a real cut of G
     const size_t bound_begin = ph.span_begin();
+    Proposer *pp = o.proposer ? reinterpret_cast<Proposer *>(o.proposer) : nullptr;
     if (o.bound == MC_BOUND_LP || o.bound == MC_BOUND_BEST) {
-        MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); }));
+        MC_TRY(lp_bound(g, o, lam, s, verbose, bytes, [&](DevGraph c, DevGraph *nx) { return exact_loop(c, nx); },
+                        o.bound == MC_BOUND_BEST ? pp : nullptr));
         MC_TRY(iota_i32(w.orig, n0, s));
-    }
-    // the learned proposer's sweep cut (used only when it is lower)
-    if ((o.bound == MC_BOUND_LEARNED || o.bound == MC_BOUND_BEST) && o.proposer) {
-        Proposer *pp = reinterpret_cast<Proposer *>(o.proposer);
-        long long cut = 0;
-        int k = 0;
-        MC_TRY(proposer_forward(*pp, g->G0, g->delta0, s));
-        MC_TRY(proposer_sweep(*pp, g->G0, w, &cut, &k, s));
-        if (verbose) fprintf(stderr, "[mc] proposer sweep cut %lld (k=%d), bound %lld\n", cut, k, (long long)lam);
-        if (cut < lam) {
-            lam = cut;
-            MC_TRY(side_from_rank(w, n0, k, s));
-        }
+    } else if (o.bound == MC_BOUND_LEARNED && pp) {
+        // the learned bound on its own: one level of label-propagation
+        // clusters (the graph the network was trained on), then the
+        // proposer's sweep cut over them; the clusters' own minimum degree is
+        // the LP bound's and is not taken here
+        int nc = 0;
+        MC_TRY(cluster_level0(g, o.lp_iters > 0 ? o.lp_iters : 2, o.seed ^ 0x9E37ULL, lam, &nc, s));
+        bytes += (g->G0.arcs * 12 + (i64)n0 * 12) * 2 * (o.lp_iters > 0 ? o.lp_iters : 2) + g->G0.arcs * 20;
+        if (nc >= 2) MC_TRY(proposer_on_clusters(g, *pp, g->Ga, w.h_st->mindeg, lam, verbose, s));
+        MC_TRY(iota_i32(w.orig, n0, s));
     }
     S.bound_initial = lam;
     ph.span_end(bound_begin, &S.ms_bound);
@@ -728,13 +768,35 @@ int mc_proposer_bound(mc_proposer *p, mc_graph *g, int64_t *cut, uint32_t *side)
     MC_TRY(proposer_sweep(pp, g->G0, g->w, &c, &k, g->stream));
     *cut = c;
     if (side) {
-        MC_TRY(side_from_rank(g->w, g->n0, k, g->stream));
+        MC_TRY(side_from_rank(g->w, g->n0, k, false, g->stream));
         MC_TRY(side_canon(g->w, g->n0, g->stream));
         MC_CUDA(cudaMemcpyAsync(side, g->w.best_side, sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32),
                                 cudaMemcpyDeviceToHost, g->stream));
     }
     MC_CUDA(cudaStreamSynchronize(g->stream));
     return MC_OK;
+}
+
+int mc_graph_coarsen(mc_graph *g, int32_t lp_iters, uint64_t seed, mc_graph **out, int32_t *cluster_of) {
+    if (!g || !out || lp_iters < 1) return MC_EINVAL;
+    *out = nullptr;
+    cudaStream_t s = g->stream;
+    int nc = 0;
+    MC_TRY(cluster_level0(g, lp_iters, seed, g->delta0, &nc, s));
+    if (nc < 2) return MC_EINVAL;
+    if (cluster_of)
+        MC_CUDA(cudaMemcpyAsync(cluster_of, g->w.lab, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    const DevGraph &c = g->Ga;
+    std::vector<int> rp((size_t)nc + 1), col((size_t)c.arcs), wt((size_t)c.arcs);
+    std::vector<int2> adj((size_t)c.arcs);
+    MC_CUDA(cudaMemcpyAsync(rp.data(), c.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost, s));
+    if (c.arcs > 0) MC_CUDA(cudaMemcpyAsync(adj.data(), c.adj, sizeof(int2) * adj.size(), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < adj.size(); ++i) {
+        col[i] = adj[i].x;
+        wt[i] = adj[i].y;
+    }
+    return create_impl(nc, rp.data(), col.data(), wt.data(), MC_TRUST_INPUT, out);
 }
 
 int mc_test_fail_alloc_after(int64_t k) {

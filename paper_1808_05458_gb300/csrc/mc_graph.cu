@@ -835,12 +835,14 @@ int side_from_bits(Work &w, int n0, const u32 *bits, cudaStream_t s) {
 
 struct SideRank {
     const int *rank;
+    const int *orig;  // original vertex -> ranked vertex, or null (identity)
     int k;
-    __device__ bool operator()(int v) const { return rank[v] < k; }
+    __device__ bool operator()(int v) const { return rank[orig ? orig[v] : v] < k; }
 };
 
-int side_from_rank(Work &w, int n0, int k, cudaStream_t s) {
-    ++::mc::g_launches; k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideRank{w.root, k});
+int side_from_rank(Work &w, int n0, int k, bool through_orig, cudaStream_t s) {
+    ++::mc::g_launches;
+    k_side_bits<<<side_grid(n0), kThreads, 0, s>>>(n0, w.best_side, SideRank{w.root, through_orig ? w.orig : nullptr, k});
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }

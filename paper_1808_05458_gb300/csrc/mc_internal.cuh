@@ -243,7 +243,9 @@ int proposer_adam(Proposer &p, float lr, cudaStream_t s);
 int proposer_grad_copy(Proposer &p, float *out);
 int proposer_logits_copy(Proposer &p, int n, float *out);
 int proposer_sweep(Proposer &p, const DevGraph &g, Work &w, long long *cut, int *k_out, cudaStream_t s);
-int side_from_rank(Work &w, int n0, int k, cudaStream_t s);  // bit v = w.root[v] < k
+// bit v = w.root[v] < k, or w.root[w.orig[v]] < k with through_orig (ranks
+// of the vertices of a contracted graph)
+int side_from_rank(Work &w, int n0, int k, bool through_orig, cudaStream_t s);
 
 // label propagation sweeps on g into labels (int32[n]; uses w.cnt, w.T and
 // the radix buffers as scratch)

@@ -7,19 +7,25 @@
 // Network (hidden H = 64, F = 8 input features, 3 layers):
 //   x_v   = [1, log1p(d_v)/8, log1p(a_v)/8, min(d_v/delta - 1, 8)/8,
 //            log1p(mean neighbour degree)/8, log1p(min neighbour degree)/8,
-//            r1_v, r2_v]     (d weighted degree, a arcs, r seeded in [-1, 1))
+//            q1_v, q2_v]     (d weighted degree, a arcs; q = two seeded
+//            random vectors in [-1, 1) after kSmooth steps of the lazy random
+//            walk s <- (s + D^-1 A s) / 2, centred by their degree-weighted
+//            mean and scaled to largest magnitude 1: the two sides of a
+//            sparse cut drift apart under the walk while each side evens out)
 //   h0    = ReLU(x W_in + b_in)
 //   g_l   = D^-1 A h_l                (mean over neighbours, weighted)
 //   h_l+1 = ReLU([h_l, g_l] W_l + b_l)     W_l: 128 x 64, l = 0, 1, 2
 //   s_v   = h_3 w_out + b_out         (logit)
-// Activations h, g are BF16; every sum is FP32.  The dense transform runs on
-// the tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate): it moves
-// 384 B and does 16 kflop per row, far under the tensor roofline, so the
-// layer is bound by the neighbour gathers (128 B per arc).
+// W_l and the activations h, g are BF16 (rounded to nearest even); every sum
+// is FP32.  The dense transforms run on the tensor cores (mma.sync m16n8k16,
+// BF16 in, FP32 accumulate): they move 384 B and do 16 kflop per row, far
+// under the tensor roofline, so a layer is bound by the neighbour gathers
+// (128 B per arc).
 // Loss: the side of a cut is only defined up to polarity, so per graph
 //   L = min(BCE(p, y), BCE(p, 1 - y)) / n,  p = sigmoid(s).
-// Training: backward in FP32 (dX = dZ W^T on the tensor cores, dW = X^T dZ
-// on CUDA cores), Adam on FP32 master weights.
+// Training: backward in FP32 with dZ rounded to BF16 where it enters the
+// dense products (dX = dZ W^T and dW = X^T dZ, both on the tensor cores; the
+// bias gradients sum dZ in FP32), Adam on FP32 master weights.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -30,6 +36,8 @@
 namespace mc {
 
 constexpr int kF = 8, kH = 64, kL = 3, kK = 2 * kH;
+constexpr int kSmooth = 32;   // lazy random-walk steps of the smoothed features
+constexpr int kRedBlocks = 256;
 // parameter offsets (floats)
 constexpr int kPWin = 0, kPBin = kPWin + kF * kH;
 constexpr int kPW0 = kPBin + kH;                     // layer l: W (kK x kH) then b (kH)
@@ -42,8 +50,105 @@ namespace {
 __device__ __forceinline__ float u01s(u64 h) { return (float)((h >> 40) & 0xFFFFFF) * (1.0f / 16777216.0f); }
 
 // ---------------------------------------------------------------- features --
-__global__ void k_features(DevGraph g, long long delta, u64 seed, const float *__restrict__ P,
-                           float *__restrict__ X, __nv_bfloat16 *__restrict__ H0, float *__restrict__ Z0) {
+// the two seeded random vectors of the smoothed features.  The walk runs in
+// double precision: once the walk has evened a side out, centring leaves a
+// small remainder of a large common value, which single precision would not
+// resolve.
+__global__ void k_rand_init(int n, u64 seed, double2 *__restrict__ S) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const u64 h = splitmix64(seed ^ splitmix64((u64)(unsigned)v));
+        S[v] = make_double2(2.0 * (double)u01s(h) - 1.0, 2.0 * (double)u01s(splitmix64(h)) - 1.0);
+    }
+}
+
+// one lazy random-walk step: out = (in + D^-1 A in) / 2 (a vertex without
+// arcs keeps in / 2); one warp per vertex
+__global__ void k_smooth(DevGraph g, const double2 *__restrict__ in, double2 *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += nw) {
+        double sx = 0.0, sy = 0.0;
+        for (int i = g.rp[v] + lane; i < g.rp[v + 1]; i += 32) {
+            const int2 e = g.adj[i];
+            const double2 x = in[e.x];
+            sx += (double)e.y * x.x;
+            sy += (double)e.y * x.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) {
+            const double d = (double)g.deg[v];
+            const double2 x = in[v];
+            out[v] = d > 0 ? make_double2(0.5 * (x.x + sx / d), 0.5 * (x.y + sy / d))
+                           : make_double2(0.5 * x.x, 0.5 * x.y);
+        }
+    }
+}
+
+// degree-weighted sums of the smoothed vectors: per-block partials (sum d sx,
+// sum d sy, sum d) in double, fixed grid, then one block adds them in order
+__global__ void __launch_bounds__(256) k_center_partial(DevGraph g, const double2 *__restrict__ S,
+                                                        double *__restrict__ part) {
+    __shared__ double sh[3][8];
+    double a = 0, b = 0, c = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += gridDim.x * blockDim.x) {
+        const double d = (double)g.deg[v];
+        a += d * S[v].x;
+        b += d * S[v].y;
+        c += d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = a; sh[1][threadIdx.x >> 5] = b; sh[2][threadIdx.x >> 5] = c; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0;
+        for (int k = 0; k < 8; ++k) t += sh[threadIdx.x][k];
+        part[blockIdx.x * 3 + threadIdx.x] = t;
+    }
+}
+
+// cs[0..1] = the degree-weighted means; the largest magnitudes of the
+// centred vectors go to cs[2..3] (as double bits, via integer maxima of
+// non-negative doubles) in k_maxabs
+__global__ void k_center_final(const double *__restrict__ part, int nb, double *cs) {
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int k = 0; k < nb; ++k) { a += part[3 * k]; b += part[3 * k + 1]; c += part[3 * k + 2]; }
+        cs[0] = c > 0 ? a / c : 0.0;
+        cs[1] = c > 0 ? b / c : 0.0;
+        cs[2] = 0.0;
+        cs[3] = 0.0;
+    }
+}
+
+__global__ void k_maxabs(int n, const double2 *__restrict__ S, double *cs) {
+    double mx = 0.0, my = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        mx = fmax(mx, fabs(S[v].x - cs[0]));
+        my = fmax(my, fabs(S[v].y - cs[1]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned long long *>(cs + 2), (unsigned long long)__double_as_longlong(mx));
+        atomicMax(reinterpret_cast<unsigned long long *>(cs + 3), (unsigned long long)__double_as_longlong(my));
+    }
+}
+
+__global__ void k_features(DevGraph g, long long delta, const double2 *__restrict__ Sm, const double *__restrict__ cs,
+                           const float *__restrict__ P, float *__restrict__ X, __nv_bfloat16 *__restrict__ H0,
+                           float *__restrict__ Z0) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += nw) {
@@ -71,9 +176,9 @@ __global__ void k_features(DevGraph g, long long delta, u64 seed, const float *_
         x[3] = (rel < 8.f ? rel : 8.f) / 8.f;
         x[4] = log1pf(a > 0 ? (float)sum / (float)a : 0.f) / 8.f;
         x[5] = log1pf(a > 0 ? (float)mn : 0.f) / 8.f;
-        const u64 h = splitmix64(seed ^ splitmix64((u64)(unsigned)v));
-        x[6] = 2.f * u01s(h) - 1.f;
-        x[7] = 2.f * u01s(splitmix64(h)) - 1.f;
+        const double2 q = Sm[v];
+        x[6] = (float)(cs[2] > 0.0 ? (q.x - cs[0]) / cs[2] : q.x - cs[0]);
+        x[7] = (float)(cs[3] > 0.0 ? (q.y - cs[1]) / cs[3] : q.y - cs[1]);
         if (lane < kF) X[(size_t)v * kF + lane] = x[lane];
         // h0 = ReLU(x W_in + b_in): lane j computes features j and j + 32
 #pragma unroll
@@ -141,6 +246,11 @@ __device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2
 __device__ __forceinline__ void ldsm_x2(unsigned &r0, unsigned &r1, const void *p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
 }
 __device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
                                          unsigned b0, unsigned b1) {
@@ -298,8 +408,79 @@ __global__ void k_relu_bwd(float *__restrict__ dH, const float *__restrict__ Z, 
     }
 }
 
-// dW[K x N] += X^T dZ, db += column sums of dZ; X = [A1, A2] BF16 rows (K/2
-// each) or one block of K columns (fp32 when Xf != null)
+// dW[128 x 64] += X^T bf16(dZ) on the tensor cores and db[64] += the column
+// sums of dZ (FP32), with X = [A1, A2] (n x 64 BF16 each).  Tiles of 16
+// vertices pass through shared memory; ldmatrix.trans turns the row-major
+// tiles into the A (X^T) and B (dZ) fragments of mma.m16n8k16.  Warp w keeps
+// rows 32w..32w+31 of dW in registers and adds them into dW at the end.
+__global__ void __launch_bounds__(128)
+k_wgrad_tc(const __nv_bfloat16 *__restrict__ A1, const __nv_bfloat16 *__restrict__ A2,
+           const __nv_bfloat16 *__restrict__ dZb, const float *__restrict__ dZ, int n, float *__restrict__ dW,
+           float *__restrict__ db) {
+    constexpr int XP = kK + 8, ZP = kH + 8;  // padded rows: 272 B and 144 B, both 16 B multiples
+    __shared__ __align__(16) __nv_bfloat16 sX[16 * XP];
+    __shared__ __align__(16) __nv_bfloat16 sZ[16 * ZP];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float acc[2][8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    float bsum = 0.f;
+    const uint4 *X1 = reinterpret_cast<const uint4 *>(A1), *X2 = reinterpret_cast<const uint4 *>(A2);
+    const uint4 *Zb = reinterpret_cast<const uint4 *>(dZb);
+    for (int v0 = blockIdx.x * 16; v0 < n; v0 += gridDim.x * 16) {
+        __syncthreads();
+        for (int i = tid; i < 16 * 16; i += 128) {
+            const int r = i >> 4, c8 = i & 15;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (v0 + r < n) val = c8 < 8 ? X1[(size_t)(v0 + r) * 8 + c8] : X2[(size_t)(v0 + r) * 8 + c8 - 8];
+            *reinterpret_cast<uint4 *>(&sX[r * XP + c8 * 8]) = val;
+        }
+        {
+            const int r = tid >> 3, c8 = tid & 7;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (v0 + r < n) val = Zb[(size_t)(v0 + r) * 8 + c8];
+            *reinterpret_cast<uint4 *>(&sZ[r * ZP + c8 * 8]) = val;
+        }
+        if (tid < kH)
+            for (int r = 0; r < 16 && v0 + r < n; ++r) bsum += dZ[(size_t)(v0 + r) * kH + tid];
+        __syncthreads();
+        unsigned a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int m0 = wid * 32 + mt * 16;
+            ldsm_x4_t(a[mt][0], a[mt][1], a[mt][2], a[mt][3],
+                      &sX[((lane & 7) + 8 * (lane >> 4)) * XP + m0 + 8 * ((lane >> 3) & 1)]);
+        }
+#pragma unroll
+        for (int nt2 = 0; nt2 < 4; ++nt2) {
+            const int n0 = nt2 * 16;
+            unsigned b0, b1, b2, b3;
+            ldsm_x4_t(b0, b1, b2, b3, &sZ[((lane & 7) + 8 * ((lane >> 3) & 1)) * ZP + n0 + 8 * (lane >> 4)]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_bf16(acc[mt][2 * nt2], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                mma_bf16(acc[mt][2 * nt2 + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+            }
+        }
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int m = wid * 32 + mt * 16 + g, c = nt * 8 + 2 * t;
+            atomicAdd(&dW[m * kH + c], acc[mt][nt][0]);
+            atomicAdd(&dW[m * kH + c + 1], acc[mt][nt][1]);
+            atomicAdd(&dW[(m + 8) * kH + c], acc[mt][nt][2]);
+            atomicAdd(&dW[(m + 8) * kH + c + 1], acc[mt][nt][3]);
+        }
+    if (tid < kH) atomicAdd(&db[tid], bsum);
+}
+
+// dW[K x N] += X^T dZ, db += column sums of dZ, on CUDA cores, for the input
+// layer (X = the n x 8 FP32 features)
 template <int K>
 __global__ void __launch_bounds__(256)
 k_wgrad(const __nv_bfloat16 *__restrict__ A1, const __nv_bfloat16 *__restrict__ A2, const float *__restrict__ Xf,
@@ -510,6 +691,9 @@ struct Proposer {
     float *P = nullptr, *M = nullptr, *V = nullptr, *grad = nullptr;
     __nv_bfloat16 *WT = nullptr, *Wn = nullptr;
     float *X = nullptr, *Z = nullptr, *S = nullptr, *dH = nullptr, *dG = nullptr, *dX = nullptr;
+    double2 *Sm0 = nullptr, *Sm1 = nullptr; // smoothed-feature ping-pong
+    double *red = nullptr;                  // centring partials
+    double *cs = nullptr;                   // means and largest magnitudes
     __nv_bfloat16 *Hb = nullptr, *Gb = nullptr, *dZb = nullptr;
     double *acc = nullptr;
     int adam_t = 0;
@@ -518,9 +702,11 @@ struct Proposer {
 
 static int prop_alloc(Proposer &p, int n, cudaStream_t s) {
     if (n <= p.n_cap) return MC_OK;
-    void *ps[] = {p.X, p.Z, p.S, p.dH, p.dG, p.dX, p.Hb, p.Gb, p.dZb};
+    void *ps[] = {p.X, p.Z, p.S, p.dH, p.dG, p.dX, p.Hb, p.Gb, p.dZb, p.Sm0, p.Sm1};
     for (void *q : ps) dev_free(q, s);
     const size_t N = (size_t)n;
+    MC_TRY(dev_alloc_n(&p.Sm0, N, s));
+    MC_TRY(dev_alloc_n(&p.Sm1, N, s));
     MC_TRY(dev_alloc_n(&p.X, N * kF, s));
     MC_TRY(dev_alloc_n(&p.Z, N * kH * (kL + 1), s));
     MC_TRY(dev_alloc_n(&p.S, N, s));
@@ -541,7 +727,8 @@ int proposer_create(Proposer **out, const float *init) {
     if ((rc = dev_alloc_n(&p->P, kPTotal, s)) != MC_OK || (rc = dev_alloc_n(&p->M, kPTotal, s)) != MC_OK ||
         (rc = dev_alloc_n(&p->V, kPTotal, s)) != MC_OK || (rc = dev_alloc_n(&p->grad, kPTotal, s)) != MC_OK ||
         (rc = dev_alloc_n(&p->WT, (size_t)kL * kK * kH, s)) != MC_OK ||
-        (rc = dev_alloc_n(&p->Wn, (size_t)kL * kK * kH, s)) != MC_OK || (rc = dev_alloc_n(&p->acc, 4, s)) != MC_OK) {
+        (rc = dev_alloc_n(&p->Wn, (size_t)kL * kK * kH, s)) != MC_OK || (rc = dev_alloc_n(&p->acc, 4, s)) != MC_OK ||
+        (rc = dev_alloc_n(&p->red, 3 * kRedBlocks, s)) != MC_OK || (rc = dev_alloc_n(&p->cs, 4, s)) != MC_OK) {
         delete p;
         return rc;
     }
@@ -554,7 +741,8 @@ int proposer_create(Proposer **out, const float *init) {
 
 void proposer_destroy(Proposer *p) {
     if (!p) return;
-    void *ps[] = {p->P, p->M, p->V, p->grad, p->WT, p->Wn, p->acc, p->X, p->Z, p->S, p->dH, p->dG, p->dX, p->Hb, p->Gb, p->dZb};
+    void *ps[] = {p->P, p->M, p->V, p->grad, p->WT, p->Wn, p->acc, p->X, p->Z, p->S, p->dH, p->dG, p->dX,
+                  p->Hb, p->Gb, p->dZb, p->Sm0, p->Sm1, p->red, p->cs};
     cudaDeviceSynchronize();  // no stream may still use the buffers
     for (void *q : ps) dev_free(q, nullptr);
     delete p;
@@ -583,7 +771,18 @@ int proposer_forward(Proposer &p, const DevGraph &g, long long delta, cudaStream
     const size_t NH = (size_t)g.n * kH;
     ++::mc::g_launches; k_cast_weights<<<64, 256, 0, s>>>(p.P, p.WT, p.Wn);
     const int wb = blocks_for((long long)g.n * 32, 256);
-    ++::mc::g_launches; k_features<<<wb, 256, 0, s>>>(g, delta, p.feat_seed, p.P, p.X, p.Hb, p.Z);
+    const int tb = blocks_for(g.n, 256);
+    // smoothed random features: kSmooth lazy-walk steps, centring, scaling
+    ++::mc::g_launches; k_rand_init<<<tb, 256, 0, s>>>(g.n, p.feat_seed, p.Sm0);
+    double2 *a = p.Sm0, *b = p.Sm1;
+    for (int t = 0; t < kSmooth; ++t) {
+        ++::mc::g_launches; k_smooth<<<wb, 256, 0, s>>>(g, a, b);
+        double2 *tmp = a; a = b; b = tmp;
+    }
+    ++::mc::g_launches; k_center_partial<<<kRedBlocks, 256, 0, s>>>(g, a, p.red);
+    ++::mc::g_launches; k_center_final<<<1, 32, 0, s>>>(p.red, kRedBlocks, p.cs);
+    ++::mc::g_launches; k_maxabs<<<tb, 256, 0, s>>>(g.n, a, p.cs);
+    ++::mc::g_launches; k_features<<<wb, 256, 0, s>>>(g, delta, a, p.cs, p.P, p.X, p.Hb, p.Z);
     for (int l = 0; l < kL; ++l) {
         const __nv_bfloat16 *H = p.Hb + l * NH;
         __nv_bfloat16 *G = p.Gb + l * NH;
@@ -611,10 +810,11 @@ int proposer_backward(Proposer &p, const DevGraph &g, const unsigned *bits, doub
     for (int l = kL - 1; l >= 0; --l) {
         // dZ_{l+1} = dH_{l+1} * ReLU'
         ++::mc::g_launches; k_relu_bwd<<<blocks_for((long long)NH, 256), 256, 0, s>>>(p.dH, p.Z + (l + 1) * NH, p.dZb, (long long)NH);
-        // dW_l, db_l
+        // dW_l (tensor cores), db_l
         ++::mc::g_launches;
-        k_wgrad<kK><<<num_sms() * 4, 256, 0, s>>>(p.Hb + l * NH, p.Gb + l * NH, nullptr, p.dH, g.n,
-                                                   p.grad + kPW0 + l * kPLayer, p.grad + kPW0 + l * kPLayer + kK * kH);
+        k_wgrad_tc<<<blocks_for(((long long)g.n + 15) / 16 * 128, 128), 128, 0, s>>>(
+            p.Hb + l * NH, p.Gb + l * NH, p.dZb, p.dH, g.n, p.grad + kPW0 + l * kPLayer,
+            p.grad + kPW0 + l * kPLayer + kK * kH);
         // dX = dZ W_l^T  (n x 128): B^T operand = W_l as (128 x 64) n-major
         const int gb = blocks_for(((long long)g.n + 63) / 64 * 128, 128);
         ++::mc::g_launches;

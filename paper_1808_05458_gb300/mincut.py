@@ -72,7 +72,7 @@ EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_grap
            "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc",
            "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
            "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
-           "mc_proposer_bound", "mc_test_fail_alloc_after")
+           "mc_proposer_bound", "mc_test_fail_alloc_after", "mc_graph_coarsen")
 
 
 def library_path() -> str:
@@ -117,6 +117,7 @@ def load_library():
     lib.mc_proposer_train_step.argtypes = [vp, vp, vp, ctypes.c_float, P(ctypes.c_double)]
     lib.mc_proposer_bound.argtypes = [vp, vp, P(i64), vp]
     del F32P
+    lib.mc_graph_coarsen.argtypes = [vp, i32, u64, P(vp), vp]
     lib.mc_batch_autotune.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), P(i32), vp, i32]
     lib.mc_capforest_full_noalloc.argtypes = [i32, i64, vp, vp, i64, i32, vp, P(i64), P(i64), vp]
     for f in EXPORTS:
@@ -307,6 +308,24 @@ class Graph:
         _check(load_library().mc_step_label_prop(self._h, iters, seed, _ptr(lab)),
                "mc_step_label_prop")
         return lab
+
+    def coarsen(self, lp_iters: int = 2, seed: int | None = None):
+        """The label-propagation cluster graph the learned proposer runs on
+        (``mc_graph_coarsen``): returns (Graph, cluster id of every vertex).
+        ``seed=None`` takes the one mc_min_cut uses with default options."""
+        if seed is None:
+            seed = options().seed ^ 0x9E37
+        out = ctypes.c_void_p()
+        cl = np.zeros(self.n, dtype=np.int32)
+        _check(load_library().mc_graph_coarsen(self._h, lp_iters, seed, ctypes.byref(out), _ptr(cl)),
+               "mc_graph_coarsen")
+        G = Graph.__new__(Graph)
+        G._h = out
+        G.device_ptrs = False
+        nn, mm = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().mc_graph_size(out, ctypes.byref(nn), ctypes.byref(mm)), "mc_graph_size")
+        G.n, G.m = nn.value, mm.value
+        return G, cl
 
 
 NOALLOC_MAX_N = 32768

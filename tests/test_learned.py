@@ -1,7 +1,8 @@
 """The learned bound proposer on the GPU against its FP64 reference.
 
-* forward logits and the full parameter gradient (BF16 activations, FP32
-  sums on the tensor cores) against oracle/gnn.py in float64;
+* forward logits and the full parameter gradient (BF16 weights and
+  activations, FP32 sums on the tensor cores) against oracle/gnn.py in
+  float64 with BF16 rounding at the same points, within 1e-2;
 * the proposed bound is an exact cut: its weight re-computed by the oracle,
   and equal to the best prefix cut of the score order computed on the host;
 * lambda never changes when the proposer supplies the bound;
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(os.path.dirname(HERE), "paper_1808_05458_gb300", "weights",
-                       "proposer_rhg16_d64.bin")
+                       "proposer_prhg16_d64.bin")
 
 
 @pytest.fixture(scope="module")
@@ -54,18 +55,22 @@ def test_forward_and_gradient_match_fp64(mc):
         with mc.Graph(*g) as G:
             logits = P.forward(G)
             loss, grad = P.grad(G, bits)
-        ref_s, _ = gnn.forward(params, *g)
-        ref_loss, ref_grad = gnn.loss_and_grad(params, *g, side.astype(np.int64))
-        assert _rel(logits, ref_s) < 2e-2, (t, _rel(logits, ref_s))
-        assert abs(loss - ref_loss) < 2e-2 * abs(ref_loss)
-        assert _rel(grad, ref_grad) < 3e-2, (t, _rel(grad, ref_grad))
+        # the reference rounds to BF16 where the kernels do, so what is left
+        # is the order of the FP32 sums (and a BF16 rounding step that the
+        # FP32 and FP64 values may take on different sides of a tie)
+        ref_s, _ = gnn.forward(params, *g, bf16_round=True)
+        ref_loss, ref_grad = gnn.loss_and_grad(params, *g, side.astype(np.int64), bf16_round=True)
+        assert _rel(logits, ref_s) < 1e-2, (t, _rel(logits, ref_s))
+        assert abs(loss - ref_loss) < 1e-2 * abs(ref_loss)
+        assert _rel(grad, ref_grad) < 1e-2, (t, _rel(grad, ref_grad))
         # every parameter block individually
         blocks = [(gnn.P_WIN, gnn.P_BIN), (gnn.P_BIN, gnn.P_W0)] + \
                  [(gnn.P_W0 + l * gnn.P_LAYER, gnn.P_W0 + (l + 1) * gnn.P_LAYER) for l in range(3)] + \
                  [(gnn.P_WOUT, gnn.P_TOTAL)]
         for a, b in blocks:
             if np.linalg.norm(ref_grad[a:b]) > 1e-6:
-                assert _rel(grad[a:b], ref_grad[a:b]) < 5e-2, (t, a, _rel(grad[a:b], ref_grad[a:b]))
+                assert _rel(grad[a:b], ref_grad[a:b]) < 1e-2, (t, a, _rel(grad[a:b], ref_grad[a:b]))
+        print(f"graph {t}: logits {_rel(logits, ref_s):.2e} grad {_rel(grad, ref_grad):.2e}")
         P.close()
 
 
@@ -123,20 +128,34 @@ def test_training_lowers_loss_and_save_load(mc, tmp_path):
     Q.close()
 
 
-@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights committed")
-def test_trained_weights_gain_report(mc):
-    # what the trained network gains over the method without it, on held-out
-    # graphs of the training family: its loss against the solver's sides is
-    # below an untrained network's, and its bound never goes below lambda
+def test_trained_network_against_the_method_without_it(mc):
+    # What the trained network gains, measured on held-out graphs of its
+    # training family (planted-cut RHG, two 2^16-point blocks, degree 64,
+    # lambda below the minimum degree): the solve with the degree bound alone
+    # (the method without it), with the label-propagation bound, and with the
+    # learned bound from trained and from untrained weights.  Lambda and its
+    # side never change; the family leaves room for a bound below the degree
+    # bound (lambda < delta), which label propagation reaches.  The learned
+    # bound is only ever a real cut (>= lambda); on this family it does not
+    # come below the degree bound, which the printed table records.
+    from paper_1808_05458_gb300 import proposer
     T = mc.Proposer.load(WEIGHTS)
     U = mc.Proposer(seed=123)
-    lt, lu = [], []
-    for seed in (900, 901):
-        g = graphgen.rhg(seed, 1 << 16, 64.0)
+    for seed in (20_000, 20_001):
+        g = proposer.planted_graph(seed, 16, 64)
+        n = len(g[0]) - 1
+        ref, _, _ = oracle.noi(*g)
         with mc.Graph(*g) as G:
-            res = G.min_cut()
-            lt.append(T.grad(G, res.bitmap)[0])
-            lu.append(U.grad(G, res.bitmap)[0])
-            cut, _ = T.bound(G)
-            assert cut >= res.lam
-    assert np.mean(lt) < np.mean(lu)
+            delta = int(G.degrees().min())
+            row = {"seed": seed, "lambda": ref, "delta": delta}
+            for name, b, P in (("degree", mc.MC_BOUND_DEGREE, None), ("lp", mc.MC_BOUND_LP, None),
+                               ("trained", mc.MC_BOUND_LEARNED, T), ("untrained", mc.MC_BOUND_LEARNED, U),
+                               ("best", mc.MC_BOUND_BEST, T)):
+                r = G.min_cut(mc.options(bound=b, proposer=P.handle if P else None))
+                assert r.lam == ref and oracle.cut_weight(*g, r.side(n)) == ref
+                row[name] = (r.stats["bound_initial"], r.stats["rounds"], round(r.stats["ms_total"], 3))
+                assert ref <= r.stats["bound_initial"] <= delta
+        assert ref < delta and row["lp"][0] == ref and row["best"][0] == ref
+        print(row)
+    T.close()
+    U.close()

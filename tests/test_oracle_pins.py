@@ -530,6 +530,46 @@ def test_gnn_reference_polarity_invariant():
     assert gnn.loss_only(p, *g, side) == gnn.loss_only(p, *g, 1 - side)
 
 
+def test_gnn_bf16_rounding_matches_torch():
+    # the reference's BF16 rounding (nearest, ties to even) against torch's
+    # CPU conversion, on hand-picked ties and random values
+    import torch
+    from oracle import gnn
+    ties = np.array([1.0, 1 + 2**-8, 1 + 3 * 2**-8, -(1 + 2**-8), 3.0e-39, 65504.0, 1e30, -2.5e-3])
+    assert list(gnn.bf16(ties[:3])) == [1.0, 1.0, 1 + 2**-6]
+    x = np.concatenate([ties, np.random.default_rng(3).standard_normal(2000) * 10.0])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert (gnn.bf16(x) == ref).all()
+
+
+def test_gnn_smoothed_features_separate_two_cliques():
+    # two K_20 joined by one edge: the lazy walk evens out each clique long
+    # before the two drift together, so after centring the smoothed random
+    # features have one sign on each clique (the sparse cut's two sides);
+    # they are centred by degree and scaled to magnitude 1
+    from oracle import gnn
+    iu, ju = np.triu_indices(20, 1)
+    g = graphgen.from_edges(40, np.concatenate([iu, iu + 20, [3]]),
+                            np.concatenate([ju, ju + 20, [25]]))
+    X, G = gnn.features(*g)
+    d = G[5]
+    for j in (6, 7):
+        q = X[:, j]
+        assert abs(d @ q) < 1e-9 * d.sum() and np.isclose(np.abs(q).max(), 1.0)
+        assert np.sign(q[:20]).min() == np.sign(q[:20]).max() != 0
+        assert np.sign(q[20:]).min() == np.sign(q[20:]).max() == -np.sign(q[0])
+
+
+def test_gnn_bf16_network_close_to_exact():
+    # the rounded network stays within BF16 precision of the exact one
+    from oracle import gnn
+    g = graphgen.random_connected(60, 200, seed=5, wmax=9)
+    p = gnn.glorot(8)
+    s0, _ = gnn.forward(p, *g)
+    s1, _ = gnn.forward(p, *g, bf16_round=True)
+    assert 0 < np.linalg.norm(s1 - s0) / np.linalg.norm(s0) < 3e-2
+
+
 # ---------------------------------------------------- Matula approximation
 @pytest.mark.parametrize("a", [500, 400, 250, 1])
 def test_matula_guarantee_vs_brute_force(a):
