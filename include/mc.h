@@ -342,7 +342,7 @@ int mc_step_label_prop(mc_graph *g, int32_t iters, uint64_t seed, int32_t *label
  *              updates, and the number of unions
  *   cuda_stream  stream to run on (NULL = default stream); the call returns
  *              after the work has finished
- * All scratch (about 3 MB) is one static device array that each GPU which
+ * All scratch (about 8 MB) is one static device array that each GPU which
  * loads the library keeps until exit.  The first call on a device looks up
  * its address (cudaGetSymbolAddress) -- make that call before any stream
  * capture.  Calls share the array: overlapping calls on one device race and

@@ -911,6 +911,7 @@ int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *lab
     cudaStream_t s = g->stream;
     ScanConfig cfg;
     cfg.start = start;
+    cfg.lam_hint = lam;
     MC_TRY(union_find_init(g->w.par, g->n0, s));
     MC_TRY(round_reset(g->w, lam, s));
     MC_TRY(capforest_full(g->G0, g->w, cfg, s));

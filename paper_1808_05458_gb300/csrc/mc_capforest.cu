@@ -250,6 +250,245 @@ k_capforest_full_bit(ScanArgs A, int start) {
     }
 }
 
+// ------------------------------------------------ block-wide full scan --
+// One thread block runs the whole full scan (Alg. 3 with the Lemma 1 cap).
+// The queue keeps, per key 0..C, a bitmap over the vertices (level 0), a
+// bitmap over level 0's words (level 1) and one over level 1's words (level
+// 2), plus a count per key and a bitmap of the keys that may hold vertices.
+// Summary bits are set when a word gains its first vertex and cleared lazily,
+// when a pop finds the word below them empty, so they are always a superset.
+// A pop takes the smallest vertex of the largest key -- the oracle's order
+// (largest key, ties to the smaller vertex) -- so the scan makes the same
+// unions as the oracle's whenever lambda-hat does not drop inside it.  The
+// popped vertex's row is spread over the block: each arc adds to r(y) (a
+// neighbour appears once per row, so r needs no atomics), tests the union
+// and moves y to its new key with atomics that only clear level-0 bits and
+// only set summary bits, so concurrent moves never lose a vertex.
+constexpr int kBlkThreads = 512;
+
+struct BlkArgs {
+    int C, W, W1, W2;
+    int *r;          // r(v), when not on chip
+    u32 *b0, *b1;    // levels 0 and 1, when not on chip
+    int on_chip;     // r, levels 0-1, row offsets and degrees in shared memory
+};
+
+__host__ __device__ inline size_t blk_smem_bytes(int n, int C, int W, int W1, int W2, bool on_chip) {
+    size_t b = (size_t)(C + 1) * W2 * 4 + (size_t)(C + 1) * 4 + 32 * 4;  // level 2, counts, key bitmap
+    if (on_chip) {
+        b += (size_t)(C + 1) * (W + W1) * 4 + 4 * (size_t)n + 4 * ((size_t)n + 1);
+        b = (b + 7) / 8 * 8 + 8 * (size_t)n;
+    }
+    return b;
+}
+
+__global__ void __launch_bounds__(kBlkThreads) k_capforest_block(ScanArgs A, int start, BlkArgs B) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ int s_x, s_a0, s_a1;
+    __shared__ long long s_L;
+    __shared__ unsigned long long s_np;
+    const int n = A.g.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int C = B.C, W = B.W, W1 = B.W1, W2 = B.W2;
+    u32 *b2 = reinterpret_cast<u32 *>(bsm);
+    int *cnt = reinterpret_cast<int *>(b2 + (size_t)(C + 1) * W2);
+    u32 *topb = reinterpret_cast<u32 *>(cnt + C + 1);
+    u32 *b0 = B.b0, *b1 = B.b1;
+    int *r = B.r;
+    const int *rp = A.g.rp;
+    const i64 *deg = A.g.deg;
+    if (B.on_chip) {
+        b0 = topb + 32;
+        b1 = b0 + (size_t)(C + 1) * W;
+        r = reinterpret_cast<int *>(b1 + (size_t)(C + 1) * W1);
+        int *rps = r + n;
+        size_t off = (size_t)(reinterpret_cast<unsigned char *>(rps + n + 1) - bsm);
+        off = (off + 7) / 8 * 8;
+        i64 *degs = reinterpret_cast<i64 *>(bsm + off);
+        for (int i = tid; i < (C + 1) * (W + W1); i += kBlkThreads) b0[i] = 0;
+        for (int v = tid; v < n; v += kBlkThreads) {
+            r[v] = 0;
+            rps[v] = A.g.rp[v];
+            degs[v] = A.g.deg[v];
+        }
+        if (tid == 0) rps[n] = A.g.rp[n];
+        rp = rps;
+        deg = degs;
+    }
+    for (int i = tid; i < (C + 1) * W2; i += kBlkThreads) b2[i] = 0;
+    for (int i = tid; i <= C; i += kBlkThreads) cnt[i] = 0;
+    if (tid < 32) topb[tid] = 0;
+    __syncthreads();
+    if (tid == 0) {
+        // the start vertex, key 0 (r, levels 0-1 off chip arrive zeroed)
+        b0[start >> 5] |= 1u << (start & 31);
+        b1[start >> 10] |= 1u << ((start >> 5) & 31);
+        b2[start >> 15] |= 1u << ((start >> 10) & 31);
+        cnt[0] = 1;
+        topb[0] = 1u;
+        s_np = 0;
+        s_L = ld_volatile_i64(&A.st->lam);
+        atomicAdd(&A.st->scan_ids, 1);
+    }
+    __syncthreads();
+    if (s_L <= 0) return;
+    long long alpha = 0, best = LLONG_MAX, arcs = 0;  // thread 0
+    int nS = 0, best_len = 0;
+    bool alpha_ok = true;
+    while (true) {
+        if (wid == 0) {
+            // pop: the smallest vertex of the largest key
+            int x = -1;
+            while (true) {
+                const u32 tw = topb[lane];
+                const unsigned m = __ballot_sync(0xffffffffu, tw != 0u);
+                if (!m) break;
+                const int wl = 31 - __clz(m);
+                const u32 twv = __shfl_sync(0xffffffffu, tw, wl);
+                const int b = wl * 32 + 31 - __clz(twv);
+                if (cnt[b] == 0) {
+                    __syncwarp();
+                    if (lane == 0) topb[b >> 5] &= ~(1u << (b & 31));
+                    __syncwarp();
+                    continue;
+                }
+                int found = -1;
+                for (int guard = 0; found < 0 && guard <= W1; ++guard) {
+                    const u32 w2 = lane < W2 ? b2[(size_t)b * W2 + lane] : 0u;
+                    const unsigned m2 = __ballot_sync(0xffffffffu, w2 != 0u);
+                    if (!m2) break;
+                    const int i2 = __ffs(m2) - 1;
+                    const int i1 = i2 * 32 + __ffs(__shfl_sync(0xffffffffu, w2, i2)) - 1;
+                    int res = -1;
+                    if (lane == 0) {
+                        u32 w1 = b1[(size_t)b * W1 + i1];
+                        while (w1) {
+                            const int i0 = i1 * 32 + __ffs(w1) - 1;
+                            const u32 w0 = b0[(size_t)b * W + i0];
+                            if (w0) {
+                                res = i0 * 32 + __ffs(w0) - 1;
+                                b0[(size_t)b * W + i0] = w0 & (w0 - 1u);
+                                break;
+                            }
+                            w1 &= w1 - 1u;  // stale summary bit: that word emptied
+                            b1[(size_t)b * W1 + i1] = w1;
+                        }
+                        if (res < 0) b2[(size_t)b * W2 + i2] &= ~(1u << (i1 & 31));
+                        else cnt[b] -= 1;
+                    }
+                    found = __shfl_sync(0xffffffffu, res, 0);
+                    __syncwarp();
+                }
+                if (found < 0) {  // a count without a vertex: an internal error
+                    if (lane == 0) atomicOr(&A.st->err, kErrNoProgress);
+                    break;
+                }
+                x = found;
+                break;
+            }
+            if (lane == 0) {
+                if (x >= 0) {
+                    const int a0 = rp[x], a1 = rp[x + 1];
+                    const long long dx = deg[x];
+                    const int rx = r[x];
+                    r[x] = kDone;
+                    A.T[x] = 1;
+                    A.order[x] = nS;
+                    ++nS;
+                    if (rx >= kSat) alpha_ok = false;
+                    alpha += dx - 2LL * rx;
+                    if (alpha_ok && nS < n && alpha < s_L) {
+                        atomicMin(&A.st->lam, alpha);
+                        best = alpha;
+                        best_len = nS;
+                        s_L = alpha;
+                    }
+                    s_a0 = a0;
+                    s_a1 = a1;
+                    arcs += a1 - a0;
+                }
+                s_x = x;
+            }
+        }
+        __syncthreads();
+        const int x = s_x;
+        if (x < 0) break;
+        const long long L = s_L;
+        const int a1 = s_a1;
+        for (int i = s_a0 + tid; i < a1; i += kBlkThreads) {
+            const int2 e = A.g.adj[i];
+            const int y = e.x;
+            const int ro = r[y];
+            if (ro == kDone) continue;
+            const int rn = sat_add(ro, e.y);
+            r[y] = rn;
+            // a certificate min(r, C) only vouches for bounds <= C
+            if ((long long)ro < L && L <= (long long)rn && L <= (long long)C) {
+                if (A.pairs) A.pairs[atomicAdd(&s_np, 1ULL)] = ((u64)(u32)x << 32) | (u32)y;
+                else if (uf_union(A.par, x, y)) atomicAdd(&s_np, 1ULL);
+            }
+            const int ko = ro == 0 ? -1 : (ro < C ? ro : C), kn = rn < C ? rn : C;
+            if (ko == kn) continue;
+            const u32 bit = 1u << (y & 31);
+            if (ko >= 0) {
+                atomicAnd(&b0[(size_t)ko * W + (y >> 5)], ~bit);
+                atomicSub(&cnt[ko], 1);
+            }
+            if (atomicOr(&b0[(size_t)kn * W + (y >> 5)], bit) == 0u &&
+                atomicOr(&b1[(size_t)kn * W1 + (y >> 10)], 1u << ((y >> 5) & 31)) == 0u)
+                atomicOr(&b2[(size_t)kn * W2 + (y >> 15)], 1u << ((y >> 10) & 31));
+            if (atomicAdd(&cnt[kn], 1) == 0) atomicOr(&topb[kn >> 5], 1u << (kn & 31));
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        A.rec_alpha[1] = best;
+        A.rec_len[1] = best_len;
+        if (A.pairs) A.st->count = (long long)s_np;
+        else atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), s_np);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)arcs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)nS);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), 1ULL);
+    }
+}
+
+// launch of the block-wide full scan; `scratch` holds (C + 1) * (W + W1)
+// words when the state does not fit on chip, r has n entries (zeroed by the
+// caller when off chip)
+int launch_full_block(const ScanArgs &A, int start, int C, int *r, u32 *scratch, size_t scratch_words,
+                      cudaStream_t s) {
+    const int n = A.g.n;
+    BlkArgs B;
+    B.C = C;
+    B.W = (n + 31) / 32;
+    B.W1 = (B.W + 31) / 32;
+    B.W2 = (B.W1 + 31) / 32;
+    const size_t on_chip_bytes = blk_smem_bytes(n, C, B.W, B.W1, B.W2, true);
+    B.on_chip = on_chip_bytes <= kBlkOnChipBytes;
+    const size_t smem = B.on_chip ? on_chip_bytes : blk_smem_bytes(n, C, B.W, B.W1, B.W2, false);
+    B.r = r;
+    B.b0 = scratch;
+    B.b1 = scratch + (size_t)(C + 1) * B.W;
+    if (!B.on_chip) {
+        if ((size_t)(C + 1) * (B.W + B.W1) > scratch_words) return MC_EINTERNAL;
+        MC_CUDA(cudaMemsetAsync(scratch, 0, sizeof(u32) * (size_t)(C + 1) * (B.W + B.W1), s));
+    }
+    static bool attr = false;
+    if (!attr) {
+        MC_CUDA(cudaFuncSetAttribute(k_capforest_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kBlkOnChipBytes));
+        attr = true;
+    }
+    ++::mc::g_launches; k_capforest_block<<<1, kBlkThreads, smem, s>>>(A, start, B);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
+size_t full_block_words(int n, int C) {
+    const size_t W = ((size_t)n + 31) / 32, W1 = (W + 31) / 32, W2 = (W1 + 31) / 32;
+    if (blk_smem_bytes(n, C, (int)W, (int)W1, (int)W2, true) <= kBlkOnChipBytes) return 0;
+    return (size_t)(C + 1) * (W + W1);
+}
+
 template <int NBK>
 static int launch_full_bit(const ScanArgs &A, int start, cudaStream_t s) {
     const size_t smem = full_bit_smem(A.g.n, NBK);
@@ -442,6 +681,24 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
     return MC_OK;
 }
 
+// The full-scan kernel for a graph and bound (off the FIFO order): one warp
+// with its whole state in shared memory for small graphs under a small cap
+// (the short rows leave a block idle, measured faster up to 8192 vertices),
+// the block-wide scan while cap and graph are within its limits, else the
+// single-warp list-queue scan.  The first two take the largest key, ties to
+// the smallest vertex.  Both entry points below pick through here, so the
+// allocating and the allocation-free scans run the same kernel.
+static int full_scan_dispatch(const ScanArgs &A, int start, long long cap, int fifo, int *r, int *eslot,
+                              int *enext, int pool, u32 *blk, size_t blk_words, cudaStream_t s) {
+    if (!fifo && cap > 0 && cap < 64 && A.g.n <= kFullBitN)
+        return cap < 16 ? launch_full_bit<16>(A, start, s) : launch_full_bit<64>(A, start, s);
+    if (!fifo && cap > 0 && cap <= kBlkMaxCap && A.g.n <= kBlkMaxN)
+        return launch_full_block(A, start, (int)cap, r, blk, blk_words, s);
+    ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, r, eslot, enext, pool, fifo);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+}
+
 int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s) {
     MC_CUDA(cudaMemsetAsync(w.T, 0, sizeof(int) * (size_t)g.n, s));
     MC_CUDA(cudaMemsetAsync(w.fb_r, 0, sizeof(int) * (size_t)g.n, s));
@@ -455,11 +712,18 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
     // key buffer; one parallel pass applies them
     A.pairs = w.keysA;
     MC_CUDA(cudaMemsetAsync(&w.st->count, 0, sizeof(w.st->count), s));
-    if (!cfg.pq_fifo && cfg.lam_hint > 0 && cfg.lam_hint < 64 && g.n <= kFullBitN) {
-        MC_TRY(cfg.lam_hint < 16 ? launch_full_bit<16>(A, start, s) : launch_full_bit<64>(A, start, s));
-    } else {
-        ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, w.fb_r, eslot, enext, (int)pool, cfg.pq_fifo);
+    const long long cap = cfg.lam_hint;
+    if (!cfg.pq_fifo && cap > 0 && cap <= kBlkMaxCap && g.n <= kBlkMaxN) {
+        const size_t words = full_block_words(g.n, (int)cap);
+        if (words > w.blk_words) {
+            dev_free(w.blk, s);
+            w.blk = nullptr;
+            w.blk_words = 0;
+            MC_TRY(dev_alloc_n(&w.blk, words, s));
+            w.blk_words = words;
+        }
     }
+    MC_TRY(full_scan_dispatch(A, start, cap, cfg.pq_fifo, w.fb_r, eslot, enext, (int)pool, w.blk, w.blk_words, s));
     {
         int blocks = (int)((g.arcs + 255) / 256);
         if (blocks > num_sms() * 4) blocks = num_sms() * 4;
@@ -472,13 +736,9 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
     return MC_OK;
 }
 
-// The full-scan kernel on caller-provided state (used by the allocation-free
-// entry point): par = union-find parents (initialised by the caller), T and
-// r zeroed, st->lam and st->scan_ids set, a pool of `pool` entries each for
-// eslot / enext.
 int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *st, i64 *rec_alpha,
-                       int *rec_len, int *r, int *eslot, int *enext, int pool, int start,
-                       cudaStream_t s) {
+                       int *rec_len, int *r, int *eslot, int *enext, int pool, u32 *blk, size_t blk_words,
+                       int start, cudaStream_t s) {
     ScanArgs A;
     A.g = g;
     A.par = par;
@@ -490,9 +750,10 @@ int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *
     A.perm_a = 1;
     A.perm_b = 0;
     A.limit = 0;
-    ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, r, eslot, enext, pool, 0);
-    MC_CUDA(cudaGetLastError());
-    return MC_OK;
+    long long cap = 0;
+    MC_CUDA(cudaMemcpyAsync(&cap, &st->lam, sizeof(cap), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    return full_scan_dispatch(A, start, cap, 0, r, eslot, enext, pool, blk, blk_words, s);
 }
 
 }  // namespace mc

@@ -73,7 +73,7 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
 void work_free(Work &w, cudaStream_t s) {
     void *ps[] = {w.par, w.root, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
                   w.valsA, w.valsB, w.radix_tmp, w.rec_alpha, w.rec_len, w.fb_r, w.fb_pool,
-                  w.best_side, w.st, w.tail};
+                  w.best_side, w.st, w.tail, w.blk};
     for (void *p : ps) dev_free(p, s);
     if (w.h_st) cudaFreeHost(w.h_st);
     w = Work();

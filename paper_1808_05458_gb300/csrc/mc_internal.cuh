@@ -145,6 +145,9 @@ struct Work {
     // single-warp tail solver scratch (allocated on first use)
     unsigned char *tail = nullptr;
     size_t tail_bytes = 0;
+    // bucket bitmaps of the block-wide full scan (allocated on first use)
+    u32 *blk = nullptr;
+    size_t blk_words = 0;
 };
 
 int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s);
@@ -210,9 +213,22 @@ int side_canon(Work &w, int n0, cudaStream_t s);
 int iota_i32(int *a, int n, cudaStream_t s);
 const std::string &error_detail();
 
+// The full scan on caller-provided state (the allocation-free entry point):
+// par = union-find parents (initialised), T and r zeroed, st->lam set, a
+// pool of `pool` entries each for eslot / enext, and `blk` (blk_words words)
+// for the block-wide scan's bucket bitmaps; unions are applied directly.
+// Picks the same kernel as capforest_full for the same graph and bound.
 int capforest_full_raw(const DevGraph &g, int *par, int *T, int *order, Status *st, i64 *rec_alpha,
-                       int *rec_len, int *r, int *eslot, int *enext, int pool, int start,
-                       cudaStream_t s);
+                       int *rec_len, int *r, int *eslot, int *enext, int pool, u32 *blk, size_t blk_words,
+                       int start, cudaStream_t s);
+// block-wide full scan limits: keys 0..kBlkMaxCap, at most kBlkMaxN
+// vertices, whole state on chip up to kBlkOnChipBytes of shared memory
+constexpr int kBlkMaxCap = 1023;
+constexpr int kBlkMaxN = 1 << 20;
+constexpr size_t kBlkOnChipBytes = 200 * 1024;
+// words of bucket bitmaps the block-wide full scan needs off chip (0 when its
+// state fits on chip)
+size_t full_block_words(int n, int cap);
 int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s);
 
 // many graphs, one warp per graph (layout of mc_batch_min_cut, host arrays);

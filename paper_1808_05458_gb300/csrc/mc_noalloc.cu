@@ -41,7 +41,9 @@ constexpr size_t kNaRecL = kNaRecA + round_up(sizeof(long long) * 2);
 constexpr size_t kNaPool = (size_t)MC_NOALLOC_MAX_ARCS + 2;
 constexpr size_t kNaSlot = kNaRecL + round_up(sizeof(int) * 2);
 constexpr size_t kNaNext = kNaSlot + round_up(sizeof(int) * kNaPool);
-constexpr size_t kNaBytes = kNaNext + round_up(sizeof(int) * kNaPool);
+constexpr size_t kNaBlkWords = (size_t)(kBlkMaxCap + 1) * (MC_NOALLOC_MAX_N / 32 + MC_NOALLOC_MAX_N / 1024);
+constexpr size_t kNaBlk = kNaNext + round_up(sizeof(int) * kNaPool);
+constexpr size_t kNaBytes = kNaBlk + round_up(sizeof(u32) * kNaBlkWords);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -178,7 +180,8 @@ extern "C" int mc_capforest_full_noalloc(int32_t n, int64_t arcs, const int32_t 
                               reinterpret_cast<int *>(base + kNaRecL),
                               reinterpret_cast<int *>(base + kNaR),
                               reinterpret_cast<int *>(base + kNaSlot),
-                              reinterpret_cast<int *>(base + kNaNext), (int)(arcs + 2), start, s));
+                              reinterpret_cast<int *>(base + kNaNext), (int)(arcs + 2),
+                              reinterpret_cast<u32 *>(base + kNaBlk), kNaBlkWords, start, s));
     MC_TRY(flatten_raw(par, labels, reinterpret_cast<int *>(base + kNaCnt), n, s));
     Status h;
     MC_CUDA(cudaMemcpyAsync(&h, st, sizeof(Status), cudaMemcpyDeviceToHost, s));

@@ -732,6 +732,43 @@ def test_full_scan_deterministic_on_ties(mc):
             assert (lab == runs[0][0]).all() and lo == runs[0][1] and un == runs[0][2]
 
 
+def _exact_full_scan_cases():
+    rng = np.random.default_rng(31)
+    cases = [_random_tiny(rng, i)[1] for i in range(120)]
+    cases += [graphgen.random_connected(400, 2500, seed=5, wmax=30),
+              graphgen.planted(3),                                  # state on chip
+              graphgen.rhg(7, 1 << 15, 24.0),                       # state off chip
+              graphgen.rmat_kcore(3, scale=16, k=24),               # a deep core, cap ~ 50
+              graphgen.cycle(2000, 3)]
+    return cases
+
+
+def test_full_scan_exact_parity_with_the_oracle(mc):
+    # The full scan takes the largest key, ties to the smallest vertex -- the
+    # oracle's order -- so while lambda-hat does not drop inside the scan its
+    # unions are the oracle's exactly (Alg. 3): at the bound lambda (no cut
+    # can lower it) from several starts, and at the bound delta whenever the
+    # scan returns it unchanged.
+    checked = 0
+    for k, g in enumerate(_exact_full_scan_cases()):
+        n = len(g[0]) - 1
+        if n < 2:
+            continue
+        deg = oracle.degrees(*g)
+        lam = oracle.noi(*g)[0] if n > 20 else oracle.brute_force(*g)[0]
+        with mc.Graph(*g) as G:
+            for bound in sorted({lam, int(deg.min())}):
+                if bound <= 0:
+                    continue
+                for start in (0, n // 2, n - 1):
+                    lab, lam_out, _ = G.capforest_full(bound, start=start)
+                    ref_lam, ref_lab = oracle.capforest_round(*g, bound, start)
+                    if lam_out == bound and ref_lam == bound:
+                        assert (lab == ref_lab).all(), (k, bound, start)
+                        checked += 1
+    assert checked > 200
+
+
 @pytest.mark.parametrize("iters", [1, 3])
 def test_label_prop_parity(mc, iters):
     # bit-exact against the oracle's reading of label propagation, on rows
