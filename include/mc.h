@@ -95,6 +95,13 @@ typedef struct mc_options {
                                 of a real cut, at most 1000 / approx_milli
                                 times lambda.  mc_min_cut only: the batched
                                 solver always solves exactly                   */
+    int32_t visits;          /* concurrent scans: how many scans may scan one
+                                vertex (Sec. 3.2 allows a vertex to be visited
+                                by several processes); 0 or 1 = once, the
+                                first scan owns it and the others blacklist it;
+                                k > 1: up to k - 1 more scans scan it, and a
+                                scan that scanned a vertex it does not own
+                                reports no further alpha cuts; at most 8      */
 } mc_options;
 
 /* Per-call statistics (all optional). The ms_* phase times come from CUDA events

@@ -369,6 +369,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
     cfg.warps = o.scans_per_round;
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
+    cfg.visits = o.visits;
     int rounds = 0, fallbacks = 0;
     const int tail_n = o.tail_vertices == 0 ? 256 : (o.tail_vertices > 4096 ? 4096 : o.tail_vertices);
     const bool verbose = getenv("MC_VERBOSE") != nullptr;
@@ -609,7 +610,9 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out, uint32_t
     if (!g || !lambda_out) return MC_EINVAL;
     mc_options o;
     if (opt) o = *opt; else mc_options_default(&o);
-    if (o.pr_level < 0 || o.pr_level > 4 || o.approx_milli < 0 || o.approx_milli > 500) return MC_EINVAL;
+    if (o.pr_level < 0 || o.pr_level > 4 || o.approx_milli < 0 || o.approx_milli > 500 || o.visits < 0 ||
+        o.visits > 8)
+        return MC_EINVAL;
     cudaStream_t s = pick_stream(g, opt);
     SolveOut so;
     int rc = solve_impl(g, o, s, so);
@@ -893,6 +896,7 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     cfg.budget = o.region_budget;
     cfg.seed = o.seed;
     cfg.lam_hint = lam;
+    cfg.visits = o.visits;
     MC_TRY(union_find_init(g->w.par, g->n0, s));
     MC_TRY(round_reset(g->w, lam, s));
     MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));

@@ -624,9 +624,11 @@ static ScanArgs make_args(const DevGraph &g, Work &w, const ScanConfig &cfg) {
 // scanned set S.  One warp would otherwise walk a hub row of 10^5 arcs alone.
 constexpr int kHubArcs = 4096;
 
-__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T, int *V) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         T[v] = rp[v + 1] - rp[v] > kHubArcs ? -1 : 0;
+        if (V) V[v] = 0;
+    }
 }
 
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s) {
@@ -634,10 +636,14 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
         int blocks = (g.n + 255) / 256;
         if (blocks > num_sms() * 16) blocks = num_sms() * 16;
         if (blocks < 1) blocks = 1;
-        ++::mc::g_launches; k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T);
+        // extra visits are counted in w.cnt, which no other step of the
+        // round uses while the scans run
+        ++::mc::g_launches; k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T, cfg.visits > 1 ? w.cnt : nullptr);
     }
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
+    A.visits = cfg.visits > 1 ? cfg.visits : 1;
+    A.V = w.cnt;
     // default region budget, measured on RHG: 192 touched vertices per scan
     // (one 256-slot table), 320 on graphs averaging >= 48 arcs per vertex;
     // 64 below 2^17 vertices, where the launch lasts as long as its longest

@@ -192,6 +192,7 @@ struct ScanConfig {
     int round = 0;
     int start = -1;        // full scan start vertex (-1 = from seed and round)
     long long lam_hint = 0; // lambda-hat at launch (selects the queue kind)
+    int visits = 1;        // scans that may scan one vertex (concurrent scans)
 };
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
 // one full CAPFOREST scan (Alg. 3) from a start vertex, single warp

@@ -218,6 +218,10 @@ struct ScanArgs {
     // of applying them (the scan never reads the union-find, so applying the
     // list afterwards gives the same partition); nullptr = apply at once
     u64 *pairs = nullptr;
+    // concurrent scans: scans a vertex may have (1 = its owner only) and the
+    // per-vertex count of the extra ones
+    int visits = 1;
+    int *V = nullptr;
 };
 
 struct Counters {
@@ -465,7 +469,7 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
         __syncwarp();
         // the row offsets and degree go out with the claim (wasted on a
         // blacklisted pop, but one round trip instead of two otherwise)
-        int old = 0;
+        int old = 0, revisit = 0;
         long long L = 0, dx = 0;
         int a0 = 0, a1 = 0;
         if (lane == 0) {
@@ -473,18 +477,27 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             a0 = A.g.rp[x];
             a1 = A.g.rp[x + 1];
             dx = A.g.deg[x];
-            if (SOLO) A.T[x] = sid;
-            else old = atomicCAS(&A.T[x], 0, sid);
+            if (SOLO) {
+                A.T[x] = sid;
+            } else {
+                old = atomicCAS(&A.T[x], 0, sid);
+                // another scan owns x: one of its visits > 1 (Sec. 3.2)?
+                if (old > 0 && A.visits > 1) revisit = atomicAdd(&A.V[x], 1) < A.visits - 1;
+            }
         }
         if (!SOLO) {
             old = __shfl_sync(0xffffffffu, old, 0);
-            if (old != 0) {
+            revisit = __shfl_sync(0xffffffffu, revisit, 0);
+            if (old != 0 && !revisit) {
                 cnt.black++;
                 continue;
             }
+            // a vertex this scan does not own is not in its recorded prefix:
+            // its later alpha values could not be traced back to a side
+            if (old != 0) alpha_ok = false;
         }
         if (lane == 0) {
-            A.order[x] = nS;
+            if (old == 0) A.order[x] = nS;
             L = L_solo;
         }
         L = __shfl_sync(0xffffffffu, L, 0);

@@ -40,7 +40,7 @@ class McOptions(ctypes.Structure):
                 ("region_budget", ctypes.c_int32), ("lp_iters", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("proposer", ctypes.c_void_p), ("tail_vertices", ctypes.c_int32),
-                ("approx_milli", ctypes.c_int32)]
+                ("approx_milli", ctypes.c_int32), ("visits", ctypes.c_int32)]
 
 
 class McStats(ctypes.Structure):
@@ -143,7 +143,7 @@ def _ptr(a):
 def options(**kw) -> McOptions:
     """Default options with overrides (pq_order, bound, pr_level,
     scans_per_round, region_budget, lp_iters, seed, cuda_stream, proposer,
-    tail_vertices, approx_milli)."""
+    tail_vertices, approx_milli, visits)."""
     o = McOptions()
     load_library().mc_options_default(ctypes.byref(o))
     for k, v in kw.items():

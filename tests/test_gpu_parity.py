@@ -181,6 +181,49 @@ def test_capforest_round_rhg_safe(mc, seed, logn, deg, unites):
         assert min(lam_out, lam_c) == lam_g
 
 
+@pytest.mark.parametrize("visits", [2, 3, 8])
+def test_capforest_round_with_revisits_safe(mc, visits):
+    # Sec. 3.2's variant where a vertex may be scanned by several scans: each
+    # scan is still a capped CAPFOREST scan of its own, so a round keeps
+    # min(lambda-hat, lambda(G/U)) = lambda(G) (Lemma 2), on tiny graphs
+    # (brute force) and on RHG graphs with thousands of concurrent scans
+    rng = np.random.default_rng(30 + visits)
+    cases = [(oracle.brute_force, _random_tiny(rng, i)[1]) for i in range(120)]
+    cases += [(lambda *g: oracle.noi(*g)[:2], graphgen.rhg(s, 1 << 14, 16.0)) for s in (2, 3)]
+    for exact, g in cases:
+        n = len(g[0]) - 1
+        if n < 3:
+            continue
+        lam_g = exact(*g)[0]
+        deg = oracle.degrees(*g)
+        for budget in (0, 6):
+            with mc.Graph(*g) as G:
+                lab, lam_out, unions = G.capforest_round(
+                    int(deg.min()), mc.options(region_budget=budget, seed=n, visits=visits))
+            assert_root_labels(lab)
+            assert lam_out >= lam_g
+            roots, lab2 = np.unique(lab, return_inverse=True)
+            if len(roots) == 1:
+                assert lam_out == lam_g
+                continue
+            crp, ccol, cw = oracle.contract(*g, lab2.astype(np.int32), len(roots))
+            cg = (crp.astype(np.int32), ccol, cw.astype(np.int32))
+            lam_c = oracle.brute_force(*cg)[0] if len(roots) <= 20 else oracle.noi(*cg)[0]
+            assert min(lam_out, lam_c) == lam_g, (n, lam_out, lam_c, lam_g)
+
+
+@pytest.mark.parametrize("visits", [2, 4])
+def test_min_cut_with_revisits(mc, visits):
+    # lambda and its side with several scans per vertex, on the plain-path
+    # workload shapes (planted blocks, RHG, an R-MAT k-core)
+    for g in (graphgen.planted(1), graphgen.rhg(3, 1 << 17, 32.0), graphgen.rmat_kcore(2, scale=17, k=10),
+              graphgen.planted_rhg(3, 1 << 15, 32.0, cross=3)):
+        ref, _, _ = oracle.noi(*g)
+        with mc.Graph(*g) as G:
+            res = G.min_cut(mc.options(visits=visits))
+        check_cut(mc, g, res, ref)
+
+
 # ------------------------------------------------------------ full solves --
 def test_random_tiny_min_cut(mc):
     rng = np.random.default_rng(4)
