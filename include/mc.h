@@ -311,6 +311,17 @@ int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels);
 int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt,
                       int32_t *labels, int64_t *lam_out, int64_t *unions_out);
 
+/* One round of concurrent capped CAPFOREST scans that scan only the vertices
+ * in [lo, hi) -- the rank-local step of the single-graph multi-GPU split:
+ * every other vertex counts as blacklisted (Sec. 3.2, Lemma 2 part 3), so
+ * it still gathers r-values and can be united, but is never scanned; its row
+ * may be empty (a rank holds only its own rows).  Outputs as
+ * mc_step_capforest, plus side_bitmap (NULL, or ceil(n/32) words): the
+ * vertices of the scan prefix whose alpha lowered the bound (all zero when
+ * none did).                                                              */
+int mc_step_capforest_range(mc_graph *g, int64_t lam, const mc_options *opt, int32_t lo, int32_t hi,
+                            int32_t *labels, int64_t *lam_out, int64_t *unions_out, uint32_t *side_bitmap);
+
 /* One full CAPFOREST scan (Alg. 3) of the whole graph from vertex `start`
  * at bound `lam`, queue capped at lam (Lemma 1): labels[v] = smallest vertex
  * of v's block after uniting every edge whose certificate crosses lam,

@@ -909,6 +909,44 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     return MC_OK;
 }
 
+int mc_step_capforest_range(mc_graph *g, int64_t lam, const mc_options *opt, int32_t lo, int32_t hi,
+                            int32_t *labels, int64_t *lam_out, int64_t *unions_out, uint32_t *side_bitmap) {
+    if (!g || !labels || lo < 0 || hi < lo || hi > g->n0) return MC_EINVAL;
+    mc_options o;
+    if (opt) o = *opt; else mc_options_default(&o);
+    cudaStream_t s = g->stream;
+    Work &w = g->w;
+    ScanConfig cfg;
+    cfg.pq_fifo = o.pq_order == MC_PQ_FIFO;
+    cfg.warps = o.scans_per_round;
+    cfg.budget = o.region_budget;
+    cfg.seed = o.seed;
+    cfg.lam_hint = lam;
+    cfg.visits = o.visits;
+    cfg.lo = lo;
+    cfg.hi = hi;
+    MC_TRY(union_find_init(w.par, g->n0, s));
+    MC_TRY(round_reset(w, lam, s));
+    MC_TRY(capforest_parallel(g->G0, w, cfg, s));
+    MC_TRY(flatten_labels(w, g->n0, s));
+    MC_TRY(status_read(w, s));
+    const Status st = *w.h_st;
+    MC_CUDA(cudaMemcpyAsync(labels, w.root, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
+    if (side_bitmap) {
+        // the prefix of the scan whose alpha lowered the bound (Sec. 3.3),
+        // over this graph's vertices; all zero when no scan lowered it
+        MC_TRY(iota_i32(w.orig, g->n0, s));
+        if (st.lam < lam && st.best_scan > 0) MC_TRY(side_from_scan(w, g->n0, st.best_scan, st.best_len, s));
+        else MC_CUDA(cudaMemsetAsync(w.best_side, 0, sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32), s));
+        MC_CUDA(cudaMemcpyAsync(side_bitmap, w.best_side, sizeof(uint32_t) * (size_t)((g->n0 + 31) / 32),
+                                cudaMemcpyDeviceToHost, s));
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (lam_out) *lam_out = st.lam;
+    if (unions_out) *unions_out = st.unions;
+    return MC_OK;
+}
+
 int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *labels, int64_t *lam_out,
                            int64_t *unions_out) {
     if (!g || !labels || start < 0 || start >= g->n0) return MC_EINVAL;

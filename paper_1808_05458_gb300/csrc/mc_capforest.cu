@@ -624,9 +624,12 @@ static ScanArgs make_args(const DevGraph &g, Work &w, const ScanConfig &cfg) {
 // scanned set S.  One warp would otherwise walk a hub row of 10^5 arcs alone.
 constexpr int kHubArcs = 4096;
 
-__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T, int *V) {
+// owners start at 0 (free) or -1 (never scanned): hubs, and the vertices
+// outside [lo, hi) when a rank scans only the vertices it owns (Sec. 3.2:
+// a vertex passed over is a blacklisted one, Lemma 2 part 3)
+__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T, int *V, int lo, int hi) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        T[v] = rp[v + 1] - rp[v] > kHubArcs ? -1 : 0;
+        T[v] = (rp[v + 1] - rp[v] > kHubArcs || v < lo || v >= hi) ? -1 : 0;
         if (V) V[v] = 0;
     }
 }
@@ -638,7 +641,9 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
         if (blocks < 1) blocks = 1;
         // extra visits are counted in w.cnt, which no other step of the
         // round uses while the scans run
-        ++::mc::g_launches; k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T, cfg.visits > 1 ? w.cnt : nullptr);
+        const int lo = cfg.lo > 0 ? cfg.lo : 0, hi = cfg.hi >= 0 && cfg.hi < g.n ? cfg.hi : g.n;
+        ++::mc::g_launches;
+        k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T, cfg.visits > 1 ? w.cnt : nullptr, lo, hi);
     }
     ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);

@@ -193,6 +193,7 @@ struct ScanConfig {
     int start = -1;        // full scan start vertex (-1 = from seed and round)
     long long lam_hint = 0; // lambda-hat at launch (selects the queue kind)
     int visits = 1;        // scans that may scan one vertex (concurrent scans)
+    int lo = 0, hi = -1;   // concurrent scans scan only vertices in [lo, hi) (hi < 0: all)
 };
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
 // one full CAPFOREST scan (Alg. 3) from a start vertex, single warp

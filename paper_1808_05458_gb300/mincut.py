@@ -72,7 +72,8 @@ EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_grap
            "mc_step_capforest_full", "mc_step_label_prop", "mc_capforest_full_noalloc",
            "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
            "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
-           "mc_proposer_bound", "mc_test_fail_alloc_after", "mc_graph_coarsen")
+           "mc_proposer_bound", "mc_test_fail_alloc_after", "mc_graph_coarsen",
+           "mc_step_capforest_range")
 
 
 def library_path() -> str:
@@ -118,6 +119,7 @@ def load_library():
     lib.mc_proposer_bound.argtypes = [vp, vp, P(i64), vp]
     del F32P
     lib.mc_graph_coarsen.argtypes = [vp, i32, u64, P(vp), vp]
+    lib.mc_step_capforest_range.argtypes = [vp, i64, P(McOptions), i32, i32, vp, P(i64), P(i64), vp]
     lib.mc_batch_autotune.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), P(i32), vp, i32]
     lib.mc_capforest_full_noalloc.argtypes = [i32, i64, vp, vp, i64, i32, vp, P(i64), P(i64), vp]
     for f in EXPORTS:
@@ -273,8 +275,9 @@ class Graph:
     def contract(self, lab, nc: int, clamp: int = 0):
         lab = np.ascontiguousarray(lab, dtype=np.int32)
         rp = np.zeros(nc + 1, dtype=np.int32)
-        col = np.zeros(max(1, 2 * self.m), dtype=np.int32)
-        w = np.zeros(max(1, 2 * self.m), dtype=np.int32)
+        # 2m + 1 arcs: a graph made with trust=True may hold an odd number
+        col = np.zeros(2 * self.m + 1, dtype=np.int32)
+        w = np.zeros(2 * self.m + 1, dtype=np.int32)
         arcs = ctypes.c_int64()
         _check(load_library().mc_step_contract(self._h, _ptr(lab), nc, clamp, _ptr(rp), _ptr(col),
                                                _ptr(w), ctypes.byref(arcs)), "mc_step_contract")
@@ -293,6 +296,18 @@ class Graph:
                                                 ctypes.byref(lo), ctypes.byref(un)),
                "mc_step_capforest")
         return lab, lo.value, un.value
+
+    def capforest_range(self, lam: int, lo: int, hi: int, opts: McOptions | None = None):
+        """(labels, lambda-hat after, unions, side bitmap) of one round of
+        concurrent scans that scan only the vertices in [lo, hi)."""
+        lab = np.zeros(self.n, dtype=np.int32)
+        side = np.zeros((self.n + 31) // 32, dtype=np.uint32)
+        lo_, un = ctypes.c_int64(), ctypes.c_int64()
+        o = opts if opts is not None else options()
+        _check(load_library().mc_step_capforest_range(self._h, lam, ctypes.byref(o), lo, hi, _ptr(lab),
+                                                      ctypes.byref(lo_), ctypes.byref(un), _ptr(side)),
+               "mc_step_capforest_range")
+        return lab, lo_.value, un.value, side
 
     def capforest_full(self, lam: int, start: int = 0):
         """One full CAPFOREST scan (Alg. 3): (labels, lambda-hat after, unions)."""
