@@ -306,12 +306,41 @@ __device__ void warp_transpose(const int *src, const int2 *adj, long long m, int
 }
 
 // Symmetry of a canonical CSR (every row free of duplicates, arcs ordered by
-// source): T1 = transpose(G) has rows sorted by source, T2 = transpose(T1) is
-// G with its rows sorted, and G is symmetric (every arc (u, v, c) has its
-// mirror (v, u, c)) exactly when T1 and T2 are equal entry for entry.
-__device__ bool warp_symmetric(const int *src, const int2 *adj, long long m, int n, int *rp1, int *src1,
-                               int2 *adj1, int *rp2, int *src2, int2 *adj2, int *cnt, int *cursor) {
+// source): G is symmetric (every arc (u, v, c) has its mirror (v, u, c))
+// exactly when every upward arc finds its mirror and as many arcs run down as
+// up (the mirror map is then a bijection).  With rows sorted by neighbour (an
+// input with sorted rows keeps them through the merge) a binary search in the
+// neighbour's row finds the mirror.  Otherwise: T1 = transpose(G) has rows
+// sorted by source, T2 = transpose(T1) is G with its rows sorted, and G is
+// symmetric exactly when T1 and T2 are equal entry for entry.
+__device__ bool warp_symmetric(const int *rp, const int *src, const int2 *adj, long long m, int n, int *rp1,
+                               int *src1, int2 *adj1, int *rp2, int *src2, int2 *adj2, int *cnt, int *cursor) {
     const int lane = lane_id();
+    bool unsorted = false;
+    for (long long i = lane; i + 1 < m; i += 32)
+        unsorted |= src[i] == src[i + 1] && adj[i].x >= adj[i + 1].x;
+    if (!__any_sync(0xffffffffu, unsorted)) {
+        bool bad = false;
+        long long up = 0, down = 0;
+        for (long long i = lane; i < m; i += 32) {
+            const int u = src[i];
+            const int2 e = adj[i];
+            if (u < e.x) {
+                ++up;
+                int lo = rp[e.x], hi = rp[e.x + 1] - 1, found = -1;
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int x = adj[mid].x;
+                    if (x == u) { found = adj[mid].y; break; }
+                    if (x < u) lo = mid + 1; else hi = mid - 1;
+                }
+                bad |= found != e.y;
+            } else {
+                ++down;
+            }
+        }
+        return !__any_sync(0xffffffffu, bad) && warp_sum_ll(up) == warp_sum_ll(down);
+    }
     warp_transpose(src, adj, m, n, rp1, src1, adj1, cnt, cursor);
     warp_transpose(src1, adj1, m, n, rp2, src2, adj2, cnt, cursor);
     bool bad = false;
@@ -517,8 +546,9 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     if (__reduce_or_sync(0xffffffffu, ovf)) err = MC_EOVERFLOW;
     // an arc without its mirror (same weight after merging) is malformed
     // input: the raw-arc buffers (B) and the sort buffers (T) are free here
-    if (!err && !warp_symmetric(S.srcA, S.adjA, arcs, n0, S.rpT, S.srcB, S.adjB, S.rpB, S.eslot, S.adjT,
-                                S.cnt, S.mark))
+    if (!err &&
+        !warp_symmetric(S.rpA, S.srcA, S.adjA, arcs, n0, S.rpT, S.srcB, S.adjB, S.rpB, S.eslot, S.adjT, S.cnt,
+                        S.mark))
         err = MC_EINVAL;
 
     long long lam = 0;

@@ -677,6 +677,20 @@ def test_batch_asymmetric_rejected(mc):
     g_par = (rp_p, np.array([1, 1, 0], dtype=np.int32), np.array([2, 3, 5], dtype=np.int32))
     lam, _, _, _ = mc.batch_min_cut(*_concat([good, g_par]))
     assert list(lam) == [8, 5]
+    # rows out of neighbour order take the transpose-based check: a
+    # symmetric graph so given is solved, an asymmetric one refused
+    def reverse_rows(g):
+        rp_, col_, w_ = (np.array(a) for a in g)
+        for v in range(len(rp_) - 1):
+            col_[rp_[v]:rp_[v + 1]] = col_[rp_[v]:rp_[v + 1]][::-1].copy()
+            w_[rp_[v]:rp_[v + 1]] = w_[rp_[v]:rp_[v + 1]][::-1].copy()
+        return rp_, col_, w_
+    rev = reverse_rows(graphgen.two_cliques(9, 2, seed=4))
+    lam, _, _, _ = mc.batch_min_cut(*_concat([rev, good]))
+    assert list(lam) == [2, 8]
+    with pytest.raises(mc.MinCutError) as ei:
+        mc.batch_min_cut(*_concat([reverse_rows((rp, col, w_bad))]))
+    assert ei.value.code == mc.MC_EINVAL
 
 
 def test_batch_4096_full(mc):
