@@ -96,7 +96,7 @@ __device__ void scan_driver(const ScanArgs &A, Counters &cnt, ScanFn scan) {
 constexpr bool kPrecheck = false;
 
 // concurrent scans with the list bucket queue (any cap)
-template <int WPB, int HC, int NB>
+template <int WPB, int HC, int NB, bool MULTI>
 __global__ void __launch_bounds__(WPB * 32)
 k_capforest(ScanArgs A, int fifo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,13 +121,13 @@ k_capforest(ScanArgs A, int fifo) {
         __syncwarp();
         q.C = (int)(L < (long long)kSat - 1 ? L : (long long)kSat - 1);
         q.coarse = q.C + 1 > NB;
-        scan_one<HashTable<HC, ScanSmem<HC, NB>>, SmemQ<HC, NB>, kPrecheck>(A, tab, q, start, sid, cnt);
+        scan_one<HashTable<HC, ScanSmem<HC, NB>>, SmemQ<HC, NB>, kPrecheck, false, MULTI>(A, tab, q, start, sid, cnt);
     });
 }
 
 // concurrent scans with the bitmap bucket queue (cap < NBK at launch; the
 // cap only falls during the launch)
-template <int WPB, int HC, int NBK>
+template <int WPB, int HC, int NBK, bool MULTI>
 __global__ void __launch_bounds__(WPB * 32)
 k_capforest_bit(ScanArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -145,7 +145,7 @@ k_capforest_bit(ScanArgs A) {
         if (lane == 0) sm.used = 0;
         __syncwarp();
         q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
-        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, kPrecheck>(A, tab, q, start, sid, cnt);
+        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, kPrecheck, false, MULTI>(A, tab, q, start, sid, cnt);
     });
 }
 
@@ -538,17 +538,17 @@ __global__ void k_scan_reset(Status *st) {
 }
 
 
-template <int WPB, int HC, int NBK>
-static int launch_parallel_bit(const ScanArgs &A, int warps_wanted, cudaStream_t s) {
+template <int WPB, int HC, int NBK, bool MULTI>
+static int launch_parallel_bit_t(const ScanArgs &A, int warps_wanted, cudaStream_t s) {
     const size_t smem = (size_t)WPB * sizeof(ScanSmemBit<HC, NBK>);
     static bool attr_set = false;
     if (!attr_set) {
-        MC_CUDA(cudaFuncSetAttribute(k_capforest_bit<WPB, HC, NBK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MC_CUDA(cudaFuncSetAttribute(k_capforest_bit<WPB, HC, NBK, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
         attr_set = true;
     }
     int per_sm = 0;
-    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest_bit<WPB, HC, NBK>, WPB * 32, smem));
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest_bit<WPB, HC, NBK, MULTI>, WPB * 32, smem));
     if (per_sm < 1) per_sm = 1;
     int blocks = per_sm * num_sms();
     if (warps_wanted > 0) {
@@ -558,22 +558,28 @@ static int launch_parallel_bit(const ScanArgs &A, int warps_wanted, cudaStream_t
     int maxb = (A.g.n + 32 * WPB - 1) / (32 * WPB);
     if (maxb < 1) maxb = 1;
     if (blocks > maxb) blocks = maxb;
-    ++::mc::g_launches; k_capforest_bit<WPB, HC, NBK><<<blocks, WPB * 32, smem, s>>>(A);
+    ++::mc::g_launches; k_capforest_bit<WPB, HC, NBK, MULTI><<<blocks, WPB * 32, smem, s>>>(A);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
 
-template <int WPB, int HC, int NB>
-static int launch_parallel(const ScanArgs &A, int fifo, int warps_wanted, cudaStream_t s) {
+template <int WPB, int HC, int NBK>
+static int launch_parallel_bit(const ScanArgs &A, int warps_wanted, cudaStream_t s) {
+    return A.visits > 1 ? launch_parallel_bit_t<WPB, HC, NBK, true>(A, warps_wanted, s)
+                        : launch_parallel_bit_t<WPB, HC, NBK, false>(A, warps_wanted, s);
+}
+
+template <int WPB, int HC, int NB, bool MULTI>
+static int launch_parallel_t(const ScanArgs &A, int fifo, int warps_wanted, cudaStream_t s) {
     const size_t smem = (size_t)WPB * sizeof(ScanSmem<HC, NB>);
     static bool attr_set = false;
     if (!attr_set) {
-        MC_CUDA(cudaFuncSetAttribute(k_capforest<WPB, HC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MC_CUDA(cudaFuncSetAttribute(k_capforest<WPB, HC, NB, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
         attr_set = true;
     }
     int per_sm = 0;
-    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest<WPB, HC, NB>, WPB * 32, smem));
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_capforest<WPB, HC, NB, MULTI>, WPB * 32, smem));
     if (per_sm < 1) per_sm = 1;
     int blocks = per_sm * num_sms();
     if (warps_wanted > 0) {
@@ -584,9 +590,15 @@ static int launch_parallel(const ScanArgs &A, int fifo, int warps_wanted, cudaSt
     int maxb = (A.g.n + 32 * WPB - 1) / (32 * WPB);
     if (maxb < 1) maxb = 1;
     if (blocks > maxb) blocks = maxb;
-    ++::mc::g_launches; k_capforest<WPB, HC, NB><<<blocks, WPB * 32, smem, s>>>(A, fifo);
+    ++::mc::g_launches; k_capforest<WPB, HC, NB, MULTI><<<blocks, WPB * 32, smem, s>>>(A, fifo);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
+}
+
+template <int WPB, int HC, int NB>
+static int launch_parallel(const ScanArgs &A, int fifo, int warps_wanted, cudaStream_t s) {
+    return A.visits > 1 ? launch_parallel_t<WPB, HC, NB, true>(A, fifo, warps_wanted, s)
+                        : launch_parallel_t<WPB, HC, NB, false>(A, fifo, warps_wanted, s);
 }
 
 static u64 gcd_u64(u64 a, u64 b) {

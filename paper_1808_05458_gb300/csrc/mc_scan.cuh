@@ -441,7 +441,9 @@ __device__ __forceinline__ bool dense_rebuild(const DenseTable &, DenseBitQ<NBK>
 // SOLO: the scan runs alone on its graph (a full scan, one warp per graph):
 // every claim succeeds, so T is written without an atomic, and lambda-hat
 // changes only through this scan, so it is kept in a register.
-template <class Table, class Q, bool PRECHECK = false, bool SOLO = false>
+// MULTI: a vertex another scan owns may still be scanned (A.visits > 1);
+// instantiated apart so the common single-visit kernels keep their registers.
+template <class Table, class Q, bool PRECHECK = false, bool SOLO = false, bool MULTI = false>
 __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid, Counters &cnt) {
     const int lane = threadIdx.x & 31;
     const int n = A.g.n;
@@ -482,19 +484,19 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
             } else {
                 old = atomicCAS(&A.T[x], 0, sid);
                 // another scan owns x: one of its visits > 1 (Sec. 3.2)?
-                if (old > 0 && A.visits > 1) revisit = atomicAdd(&A.V[x], 1) < A.visits - 1;
+                if (MULTI && old > 0) revisit = atomicAdd(&A.V[x], 1) < A.visits - 1;
             }
         }
         if (!SOLO) {
             old = __shfl_sync(0xffffffffu, old, 0);
-            revisit = __shfl_sync(0xffffffffu, revisit, 0);
+            if (MULTI) revisit = __shfl_sync(0xffffffffu, revisit, 0);
             if (old != 0 && !revisit) {
                 cnt.black++;
                 continue;
             }
             // a vertex this scan does not own is not in its recorded prefix:
             // its later alpha values could not be traced back to a side
-            if (old != 0) alpha_ok = false;
+            if (MULTI && old != 0) alpha_ok = false;
         }
         if (lane == 0) {
             if (old == 0) A.order[x] = nS;
