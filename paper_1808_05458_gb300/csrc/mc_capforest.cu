@@ -271,10 +271,13 @@ struct BlkArgs {
     int *r;          // r(v), when not on chip
     u32 *b0, *b1;    // levels 0 and 1, when not on chip
     int on_chip;     // r, levels 0-1, row offsets and degrees in shared memory
+    int b1_on_chip;  // otherwise: level 1 in shared memory still (it is small)
 };
 
-__host__ __device__ inline size_t blk_smem_bytes(int n, int C, int W, int W1, int W2, bool on_chip) {
+__host__ __device__ inline size_t blk_smem_bytes(int n, int C, int W, int W1, int W2, bool on_chip,
+                                                 bool b1_on_chip = false) {
     size_t b = (size_t)(C + 1) * W2 * 4 + (size_t)(C + 1) * 4 + 32 * 4;  // level 2, counts, key bitmap
+    if (!on_chip && b1_on_chip) b += (size_t)(C + 1) * W1 * 4;
     if (on_chip) {
         b += (size_t)(C + 1) * (W + W1) * 4 + 4 * (size_t)n + 4 * ((size_t)n + 1);
         b = (b + 7) / 8 * 8 + 8 * (size_t)n;
@@ -313,6 +316,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_capforest_block(ScanArgs A, int
         if (tid == 0) rps[n] = A.g.rp[n];
         rp = rps;
         deg = degs;
+    } else if (B.b1_on_chip) {
+        b1 = topb + 32;
+        for (int i = tid; i < (C + 1) * W1; i += kBlkThreads) b1[i] = 0;
     }
     for (int i = tid; i < (C + 1) * W2; i += kBlkThreads) b2[i] = 0;
     for (int i = tid; i <= C; i += kBlkThreads) cnt[i] = 0;
@@ -464,7 +470,8 @@ int launch_full_block(const ScanArgs &A, int start, int C, int *r, u32 *scratch,
     B.W2 = (B.W1 + 31) / 32;
     const size_t on_chip_bytes = blk_smem_bytes(n, C, B.W, B.W1, B.W2, true);
     B.on_chip = on_chip_bytes <= kBlkOnChipBytes;
-    const size_t smem = B.on_chip ? on_chip_bytes : blk_smem_bytes(n, C, B.W, B.W1, B.W2, false);
+    B.b1_on_chip = !B.on_chip && blk_smem_bytes(n, C, B.W, B.W1, B.W2, false, true) <= kBlkOnChipBytes;
+    const size_t smem = B.on_chip ? on_chip_bytes : blk_smem_bytes(n, C, B.W, B.W1, B.W2, false, B.b1_on_chip);
     B.r = r;
     B.b0 = scratch;
     B.b1 = scratch + (size_t)(C + 1) * B.W;
