@@ -194,58 +194,175 @@ k_capforest_full(ScanArgs A, int start, int *r, int *eslot, int *enext, int pool
     }
 }
 
-// full scan of a small graph with a small cap: the r-values, the row
-// offsets, the degrees and a dense bitmap queue all in shared memory
-constexpr int kFullBitN = 8192;
+// Full scan of a small graph with a small cap (Alg. 3, n <= 8192, key cap
+// C <= 63) on one warp: r, the row offsets, the degrees and one bitmap per key
+// over the vertices in shared memory.  A pop takes the smallest vertex of the
+// largest key, the oracle's order, so the unions are the oracle's whenever
+// lambda-hat does not drop inside the scan.  A queue entry packs into one
+// word, (key + 1) << 13 | (8191 - vertex), so the entry to pop is a maximum:
+// * once x is popped and before its row is applied, the candidate q (the
+//   largest entry left) is searched while x's row is on its way; the row only
+//   raises keys, so the next pop is the larger of q and the row's largest
+//   move, one warp reduction per 32 arcs and no second search;
+// * q's first 32 arcs are loaded one pop ahead and used when q is indeed the
+//   next pop (about two pops in three on random and hyperbolic graphs).
+// The dependent chain per pop is a few shared-memory loads, one search and
+// one reduction per chunk of arcs.
+constexpr int kSmallN = 8192;
+constexpr int kSmallMaxC = 63;
 
-__host__ __device__ inline size_t full_bit_smem(int n, int nbk) {
-    const size_t W = ((size_t)n + 31) / 32;
-    size_t b = 4 * (size_t)n + 4 * ((size_t)n + 1);
-    b = (b + 7) / 8 * 8;
-    return b + 8 * (size_t)n + 4 * (size_t)nbk * W + 4 * (size_t)nbk;
+__host__ __device__ inline size_t small_scan_smem(int n, int C, int kw) {
+    return (size_t)(C + 1) * 32 * kw * 4 + 8 * (size_t)n + 4 * (size_t)n + 4 * ((size_t)n + 1);
 }
 
-template <int NBK>
-__global__ void __launch_bounds__(32)
-k_capforest_full_bit(ScanArgs A, int start) {
-    extern __shared__ __align__(16) unsigned char fsm[];
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ unsigned small_entry(int key, int v) {
+    return ((unsigned)(key + 1) << 13) | (unsigned)(kSmallN - 1 - v);
+}
+
+template <int KW>  // bitmap words per lane and key: 32 * KW words cover the vertices
+__global__ void __launch_bounds__(32) k_capforest_small(ScanArgs A, int start, int Cmax) {
+    extern __shared__ __align__(16) unsigned char ssm[];
+    constexpr unsigned kAll = 0xffffffffu;
+    constexpr int Wp = 32 * KW;
+    const int lane = threadIdx.x;
     const int n = A.g.n;
-    const int W = (n + 31) / 32;
-    int *r = reinterpret_cast<int *>(fsm);
-    int *rp = r + n;
-    size_t off = 4 * (size_t)n + 4 * ((size_t)n + 1);
-    off = (off + 7) / 8 * 8;
-    long long *deg = reinterpret_cast<long long *>(fsm + off);
-    u32 *bits = reinterpret_cast<u32 *>(deg + n);
-    int *cnt = reinterpret_cast<int *>(bits + (size_t)NBK * W);
-    for (int v = lane; v < n; v += 32) { r[v] = 0; rp[v] = A.g.rp[v]; deg[v] = A.g.deg[v]; }
-    if (lane == 0) rp[n] = A.g.rp[n];
-    for (int i = lane; i < NBK * W; i += 32) bits[i] = 0;
-    for (int i = lane; i < NBK; i += 32) cnt[i] = 0;
-    __syncwarp();
-    const long long L = ld_volatile_i64(&A.st->lam);
-    if (L <= 0) return;
-    DenseBitQ<NBK> q;
-    q.bits = bits;
-    q.cnt = cnt;
-    q.W = W;
-    q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
-    DenseTable tab{r, 0};
-    ScanArgs B = A;
-    B.g.rp = rp;
-    B.g.deg = deg;
-    Counters c;
+    const long long L0 = ld_volatile_i64(&A.st->lam);
     if (lane == 0) atomicAdd(&A.st->scan_ids, 1);
-    scan_one<DenseTable, DenseBitQ<NBK>, false, true>(B, tab, q, start, 1, c);
-    if (lane == 0) A.st->count = c.npairs;
-    long long un = c.unions;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+    if (L0 <= 0) return;
+    const int C = (int)(L0 < Cmax ? L0 : Cmax);  // Cmax sized the shared memory
+    u32 *b0 = reinterpret_cast<u32 *>(ssm);      // (C + 1) x Wp, key-major
+    long long *deg = reinterpret_cast<long long *>(b0 + (size_t)(C + 1) * Wp);
+    int *r = reinterpret_cast<int *>(deg + n);
+    int *rp = r + n;
+    for (int i = lane; i < (C + 1) * Wp; i += 32) b0[i] = 0;
+    for (int v = lane; v < n; v += 32) { r[v] = 0; rp[v] = A.g.rp[v]; deg[v] = A.g.deg[v]; }
     if (lane == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), (unsigned long long)un);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)c.arcs);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)c.verts);
+        rp[n] = A.g.rp[n];
+        b0[start >> 5] = 1u << (start & 31);
+    }
+    __syncwarp();
+
+    // the largest entry, keys above `top` being empty; lowers top past the
+    // keys it finds empty; 0 = none
+    int top = 0;
+    auto search = [&]() -> unsigned {
+        for (; top >= 0; --top) {
+            const uint4 *row = reinterpret_cast<const uint4 *>(b0 + (size_t)top * Wp + lane * KW);
+            int v = INT_MAX;
+#pragma unroll
+            for (int j = KW / 4 - 1; j >= 0; --j) {
+                const uint4 q = row[j];
+                const int base = (lane * KW + 4 * j) * 32 - 1;
+                if (q.w) v = base + 96 + __ffs(q.w);
+                if (q.z) v = base + 64 + __ffs(q.z);
+                if (q.y) v = base + 32 + __ffs(q.y);
+                if (q.x) v = base + __ffs(q.x);
+            }
+            v = (int)__reduce_min_sync(kAll, (unsigned)v);
+            if (v != INT_MAX) return small_entry(top, v);
+        }
+        top = 0;
+        return 0u;
+    };
+
+    long long L = L0, alpha = 0, best = LLONG_MAX, arcs = 0, npairs = 0;
+    int Lj = L <= C ? (int)L : INT_MAX;  // L as the join threshold (no join above C)
+    int nS = 0, best_len = 0, unions = 0;
+    bool alpha_ok = true;
+    unsigned pe = search();
+    int spec_v = -1;
+    int2 spec_e = make_int2(0, 0);
+    while (pe != 0u) {
+        if (nS >= n) {  // every vertex popped already: an internal error
+            if (lane == 0) atomicOr(&A.st->err, kErrNoProgress);
+            break;
+        }
+        const int p = kSmallN - 1 - (int)(pe & (kSmallN - 1)), Kp = (int)(pe >> 13) - 1;
+        const int a0 = rp[p], a1 = rp[p + 1];
+        const int rx = r[p];
+        const long long dx = deg[p];
+        // p's first chunk: loaded one pop ahead, or now
+        int2 e = spec_e;
+        if (p != spec_v) e = a0 + lane < a1 ? A.g.adj[a0 + lane] : make_int2(0, 0);
+        if (lane == 0) {
+            b0[(size_t)Kp * Wp + (p >> 5)] &= ~(1u << (p & 31));
+            r[p] = kDone;
+            A.T[p] = 1;
+            A.order[p] = nS;
+        }
+        __syncwarp();
+        ++nS;
+        if (rx >= kSat) alpha_ok = false;
+        alpha += dx - 2LL * rx;
+        if (alpha_ok && nS < n && alpha < L) {
+            if (lane == 0) atomicMin(&A.st->lam, alpha);
+            best = alpha;
+            best_len = nS;
+            L = alpha;
+            Lj = L <= C ? (int)L : INT_MAX;
+        }
+        arcs += a1 - a0;
+        // the candidate before p's row is applied, and its first chunk
+        const unsigned qe = search();
+        spec_v = kSmallN - 1 - (int)(qe & (kSmallN - 1));
+        if (qe != 0u) {
+            const int qa0 = rp[spec_v], qa1 = rp[spec_v + 1];
+            spec_e = qa0 + lane < qa1 ? A.g.adj[qa0 + lane] : make_int2(0, 0);
+        } else {
+            spec_v = -1;
+        }
+        __syncwarp();  // the search reads the bitmaps before p's moves change them
+        unsigned be = qe;  // the next pop: the candidate or a larger move
+        int xh = p;
+        for (int i0 = a0; i0 < a1; i0 += 32) {
+            if (i0 != a0) e = i0 + lane < a1 ? A.g.adj[i0 + lane] : make_int2(0, 0);
+            const int y = e.x;
+            unsigned me = 0u;
+            bool join = false;
+            if (i0 + lane < a1) {
+                const int ro = r[y];
+                if (ro != kDone) {
+                    const int rn = sat_add(ro, e.y);
+                    r[y] = rn;
+                    // a certificate min(r, C) only vouches for bounds <= C
+                    join = ro < Lj && Lj <= rn;
+                    const int ko = ro == 0 ? -1 : (ro < C ? ro : C), kn = rn < C ? rn : C;
+                    if (ko != kn) {
+                        const u32 bit = 1u << (y & 31);
+                        if (ko >= 0) atomicAnd(&b0[(size_t)ko * Wp + (y >> 5)], ~bit);
+                        atomicOr(&b0[(size_t)kn * Wp + (y >> 5)], bit);
+                        me = small_entry(kn, y);
+                    }
+                }
+            }
+            if (A.pairs) {
+                const unsigned jm = __ballot_sync(kAll, join);
+                if (join) A.pairs[npairs + __popc(jm & ((1u << lane) - 1u))] = ((u64)(u32)p << 32) | (u32)y;
+                npairs += __popc(jm);
+            } else {
+                int rt = INT_MAX;
+                if (join && uf_union_root(A.par, xh, y, &rt)) ++unions;
+                rt = __reduce_min_sync(kAll, rt);
+                if (rt != INT_MAX) xh = rt;
+            }
+            me = __reduce_max_sync(kAll, me);
+            be = me > be ? me : be;
+        }
+        const int kb = (int)(be >> 13) - 1;
+        top = kb > top ? kb : top;
+        pe = be;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        A.rec_alpha[1] = best;
+        A.rec_len[1] = best_len;
+        if (A.pairs) A.st->count = npairs;
+    }
+    unions = (int)__reduce_add_sync(kAll, (unsigned)unions);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->unions), (unsigned long long)unions);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_arcs), (unsigned long long)arcs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scanned_verts), (unsigned long long)nS);
         atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->scans), 1ULL);
     }
 }
@@ -496,18 +613,22 @@ size_t full_block_words(int n, int C) {
     return (size_t)(C + 1) * (W + W1);
 }
 
-template <int NBK>
-static int launch_full_bit(const ScanArgs &A, int start, cudaStream_t s) {
-    const size_t smem = full_bit_smem(A.g.n, NBK);
+template <int KW>
+static int launch_small_t(const ScanArgs &A, int start, int C, cudaStream_t s) {
+    const size_t smem = small_scan_smem(A.g.n, C, KW);
     static bool attr = false;
     if (!attr) {
-        MC_CUDA(cudaFuncSetAttribute(k_capforest_full_bit<NBK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)full_bit_smem(kFullBitN, 64)));
+        MC_CUDA(cudaFuncSetAttribute(k_capforest_small<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)small_scan_smem(kSmallN, kSmallMaxC, 8)));
         attr = true;
     }
-    ++::mc::g_launches; k_capforest_full_bit<NBK><<<1, 32, smem, s>>>(A, start);
+    ++::mc::g_launches; k_capforest_small<KW><<<1, 32, smem, s>>>(A, start, C);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
+}
+
+static int launch_small(const ScanArgs &A, int start, int C, cudaStream_t s) {
+    return A.g.n <= 32 * 32 * 4 ? launch_small_t<4>(A, start, C, s) : launch_small_t<8>(A, start, C, s);
 }
 
 // the unions a lone scan recorded (st->count pairs), counted into st->unions
@@ -718,10 +839,13 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
 // single-warp list-queue scan.  The first two take the largest key, ties to
 // the smallest vertex.  Both entry points below pick through here, so the
 // allocating and the allocation-free scans run the same kernel.
+bool full_scan_is_small(int n, long long cap, bool fifo) {
+    return !fifo && cap > 0 && cap <= kSmallMaxC && n <= kSmallN;
+}
+
 static int full_scan_dispatch(const ScanArgs &A, int start, long long cap, int fifo, int *r, int *eslot,
                               int *enext, int pool, u32 *blk, size_t blk_words, cudaStream_t s) {
-    if (!fifo && cap > 0 && cap < 64 && A.g.n <= kFullBitN)
-        return cap < 16 ? launch_full_bit<16>(A, start, s) : launch_full_bit<64>(A, start, s);
+    if (full_scan_is_small(A.g.n, cap, fifo != 0)) return launch_small(A, start, (int)cap, s);
     if (!fifo && cap > 0 && cap <= kBlkMaxCap && A.g.n <= kBlkMaxN)
         return launch_full_block(A, start, (int)cap, r, blk, blk_words, s);
     ++::mc::g_launches; k_capforest_full<<<1, 32, 0, s>>>(A, start, r, eslot, enext, pool, fifo);

@@ -198,6 +198,9 @@ struct ScanConfig {
 int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
 // one full CAPFOREST scan (Alg. 3) from a start vertex, single warp
 int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream_t s);
+// true when capforest_full runs the one-warp scan of a small graph (n <= 8192,
+// bound <= 63, largest-key order), whose cost is a few wide scans'
+bool full_scan_is_small(int n, long long cap, bool fifo);
 
 // side bitmaps (original vertex ids, n0 bits)
 int side_from_vertex(Work &w, int n0, int vertex, cudaStream_t s);

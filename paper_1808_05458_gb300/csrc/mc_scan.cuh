@@ -365,74 +365,6 @@ __device__ __forceinline__ int q_pop(BitQ<HC, NBK> &q, const int *) {
     return s;
 }
 
-// Bitmap bucket queue over a dense slot range [0, n) (full scans of small
-// graphs): bucket b is a bitmap of W = ceil(n / 32) words plus a count, as in
-// BitQ, with W a run-time size; a pop searches the top bucket's words 32 at a
-// time.  Needs C < NBK.
-template <int NBK>
-struct DenseBitQ {
-    u32 *bits;  // NBK x W words
-    int *cnt;   // NBK counts
-    int W;
-    int C;
-    bool coarse = false;
-    __device__ __forceinline__ int bucket(int k) const { return k; }
-};
-template <int NBK>
-__device__ __forceinline__ bool q_changed(const DenseBitQ<NBK> &q, int ko, int kn) {
-    return ko != kn;
-}
-template <int NBK>
-__device__ __forceinline__ bool q_update(DenseBitQ<NBK> &q, bool want, int s, int ko, int kn) {
-    if (want) {
-        const u32 bit = 1u << (s & 31);
-        const int wd = s >> 5;
-        if (ko >= 0) {
-            atomicAnd(&q.bits[ko * q.W + wd], ~bit);
-            atomicSub(&q.cnt[ko], 1);
-        }
-        atomicOr(&q.bits[kn * q.W + wd], bit);
-        atomicAdd(&q.cnt[kn], 1);
-    }
-    __syncwarp();
-    return true;
-}
-template <int NBK>
-__device__ __forceinline__ int q_pop(DenseBitQ<NBK> &q, const int *) {
-    static_assert(NBK <= 64, "dense bitmap queue bounds");
-    const int lane = threadIdx.x & 31;
-    int top = -1;
-#pragma unroll
-    for (int b0 = ((NBK - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
-        const int b = b0 + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, b < NBK && b <= q.C && q.cnt[b] > 0);
-        if (top < 0 && m) top = b0 + 31 - __clz(m);
-    }
-    if (top < 0) return -1;
-    const u32 *row = q.bits + (size_t)top * q.W;
-    int s = -1;
-    for (int w0 = 0; w0 < q.W && s < 0; w0 += 32) {
-        const u32 word = w0 + lane < q.W ? row[w0 + lane] : 0u;
-        const unsigned m = __ballot_sync(0xffffffffu, word != 0u);
-        if (m) {
-            const int wl = __ffs(m) - 1;
-            const u32 wv = __shfl_sync(0xffffffffu, word, wl);
-            s = (w0 + wl) * 32 + __ffs(wv) - 1;
-        }
-    }
-    __syncwarp();
-    if (lane == 0 && s >= 0) {
-        q.bits[(size_t)top * q.W + (s >> 5)] &= ~(1u << (s & 31));
-        q.cnt[top] -= 1;
-    }
-    __syncwarp();
-    return s;
-}
-template <int NBK>
-__device__ __forceinline__ bool dense_rebuild(const DenseTable &, DenseBitQ<NBK> &) {
-    return true;  // never out of room
-}
-
 // A scan with PRECHECK looks up the owner of every vertex it touches for the
 // first time: a vertex another scan already owns is blacklisted right away
 // (Alg. 1's blacklisting, taken before any of its arcs count, so it never

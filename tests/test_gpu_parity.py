@@ -793,8 +793,11 @@ def _exact_full_scan_cases():
     rng = np.random.default_rng(31)
     cases = [_random_tiny(rng, i)[1] for i in range(120)]
     cases += [graphgen.random_connected(400, 2500, seed=5, wmax=30),
-              graphgen.planted(3),                                  # state on chip
-              graphgen.rhg(7, 1 << 15, 24.0),                       # state off chip
+              graphgen.planted(3),                                  # one-warp scan, n <= 4096
+              graphgen.planted(5, block_n=3000, avg_deg=40.0, cross=6),  # n 6000, rows of 3 chunks
+              graphgen.random_gnp(200, 0.2, seed=21, wmax=2),       # cap 40, rows of 2 chunks
+              graphgen.planted(6, block_n=5000, avg_deg=16.0, cross=4),  # block scan, state on chip
+              graphgen.rhg(7, 1 << 15, 24.0),                       # block scan, state off chip
               graphgen.rmat_kcore(3, scale=16, k=24),               # a deep core, cap ~ 50
               graphgen.cycle(2000, 3)]
     return cases
