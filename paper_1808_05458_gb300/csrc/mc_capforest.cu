@@ -133,19 +133,13 @@ k_capforest_bit(ScanArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     ScanSmemBit<HC, NBK> &sm = reinterpret_cast<ScanSmemBit<HC, NBK> *>(smem_raw)[threadIdx.x >> 5];
-    HashTable<HC, ScanSmemBit<HC, NBK>> tab{&sm, A.limit};
-    BitQ<HC, NBK> q;
-    q.bits = sm.bits;
-    q.cnt = sm.cnt;
     Counters cnt;
     scan_driver(A, cnt, [&](int start, int sid, long long L) {
         for (int i = lane; i < HC; i += 32) sm.key[i] = -1;
         for (int i = lane; i < NBK * (HC / 32); i += 32) sm.bits[i] = 0;
-        for (int i = lane; i < NBK; i += 32) sm.cnt[i] = 0;
         if (lane == 0) sm.used = 0;
         __syncwarp();
-        q.C = (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1);
-        scan_one<HashTable<HC, ScanSmemBit<HC, NBK>>, BitQ<HC, NBK>, kPrecheck, false, MULTI>(A, tab, q, start, sid, cnt);
+        scan_bit<HC, NBK, MULTI>(A, sm, (int)(L < (long long)NBK - 1 ? L : (long long)NBK - 1), start, sid, cnt);
     });
 }
 

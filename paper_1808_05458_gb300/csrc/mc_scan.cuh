@@ -224,9 +224,10 @@ struct ScanArgs {
     int *V = nullptr;
 };
 
+// per-warp totals of one launch (each is at most the graph's arc count, < 2^31)
 struct Counters {
-    long long arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
-    long long npairs = 0;  // unions recorded in ScanArgs::pairs
+    int arcs = 0, verts = 0, unions = 0, black = 0, scans = 0;
+    int npairs = 0;  // unions recorded in ScanArgs::pairs
 };
 
 // garbage-collect a hash table's queue: rebuild every bucket list from the
@@ -302,67 +303,6 @@ __device__ __forceinline__ bool q_update(BucketQ<Idx, NB> &q, bool want, int s, 
 template <class Idx, int NB>
 __device__ __forceinline__ int q_pop(BucketQ<Idx, NB> &q, const int *rv) {
     return pq_pop(q, rv);
-}
-
-// Bitmap bucket queue for small caps (C < NBK <= 64) over a table of HC <=
-// 1024 slots: bucket b is a bitmap of its slots plus a member count.  A key
-// change clears the slot's bit in the old bucket and sets it in the new one,
-// so the queue never holds stale entries; a pop takes the lowest slot of the
-// highest non-empty bucket (a fixed tie rule, like LIFO/FIFO any order among
-// equal keys is valid).
-template <int HC, int NBK>
-struct BitQ {
-    static constexpr int W = HC / 32;
-    u32 *bits;  // NBK x W words
-    int *cnt;   // NBK counts
-    int C;
-    bool coarse = false;
-    __device__ __forceinline__ int bucket(int k) const { return k; }
-};
-template <int HC, int NBK>
-__device__ __forceinline__ bool q_changed(const BitQ<HC, NBK> &q, int ko, int kn) {
-    return ko != kn;
-}
-template <int HC, int NBK>
-__device__ __forceinline__ bool q_update(BitQ<HC, NBK> &q, bool want, int s, int ko, int kn) {
-    if (want) {
-        const u32 bit = 1u << (s & 31);
-        const int wd = s >> 5;
-        if (ko >= 0) {
-            atomicAnd(&q.bits[ko * BitQ<HC, NBK>::W + wd], ~bit);
-            atomicSub(&q.cnt[ko], 1);
-        }
-        atomicOr(&q.bits[kn * BitQ<HC, NBK>::W + wd], bit);
-        atomicAdd(&q.cnt[kn], 1);
-    }
-    __syncwarp();
-    return true;
-}
-template <int HC, int NBK>
-__device__ __forceinline__ int q_pop(BitQ<HC, NBK> &q, const int *) {
-    static_assert(HC / 32 <= 32 && NBK <= 64, "bitmap queue bounds");
-    const int lane = threadIdx.x & 31;
-    int top = -1;
-#pragma unroll
-    for (int b0 = ((NBK - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
-        const int b = b0 + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, b < NBK && b <= q.C && q.cnt[b] > 0);
-        if (top < 0 && m) top = b0 + 31 - __clz(m);
-    }
-    if (top < 0) return -1;
-    constexpr int W = BitQ<HC, NBK>::W;
-    const u32 word = lane < W ? q.bits[top * W + lane] : 0u;
-    const unsigned m = __ballot_sync(0xffffffffu, word != 0u);
-    const int wl = __ffs(m) - 1;
-    const u32 wv = __shfl_sync(0xffffffffu, word, wl);
-    const int s = wl * 32 + __ffs(wv) - 1;
-    __syncwarp();
-    if (lane == 0) {
-        q.bits[top * W + wl] = wv & (wv - 1u);
-        q.cnt[top] -= 1;
-    }
-    __syncwarp();
-    return s;
 }
 
 // A scan with PRECHECK looks up the owner of every vertex it touches for the
@@ -511,15 +451,183 @@ __device__ void scan_one(const ScanArgs &A, Table &tab, Q &q, int start, int sid
     }
 }
 
-// shared memory of one warp's scan with the bitmap queue
+// shared memory of one warp's scan with the bitmap queue: per key, a bitmap
+// over the table's slots
 template <int HC, int NBK>
 struct ScanSmemBit {
     int key[HC];
     int val[HC];
     u32 bits[NBK * (HC / 32)];
-    int cnt[NBK];
     int used;
 };
+
+// One capped scan (Alg. 1) of the concurrent rounds with the bitmap queue
+// (HC <= 1024 table slots, keys 0..C, C < NBK <= 64): the steps of scan_one
+// for a hash table, blacklisting at the pop, with the per-pop chain of
+// dependent latencies cut three ways:
+// * a queue entry packs into one word, (key + 1) << 10 | (1023 - slot), so the
+//   next pop is a maximum: the candidate searched once the popped vertex is
+//   removed and before its row is applied, or the row's largest move (keys
+//   only rise), one warp reduction per 32 arcs and no search after the row;
+// * the candidate's row offsets and owner are loaded one pop ahead: when it
+//   is popped its claim and its first 32 arcs leave together;
+// * a candidate some other scan owned already when it was looked up is
+//   blacklisted at its pop without a claim (ownership never reverts within a
+//   round, so the claim would fail); with several visits the claim is kept,
+//   it also counts the visits.
+// A pop takes a largest key, ties to the lowest slot, as Alg. 1 allows.
+template <int HC, int NBK, bool MULTI>
+__device__ void scan_bit(const ScanArgs &A, ScanSmemBit<HC, NBK> &sm, int C, int start, int sid, Counters &cnt) {
+    static_assert(HC <= 1024 && HC % 32 == 0 && HC / 32 <= 32 && NBK <= 64, "bitmap queue bounds");
+    constexpr unsigned kAll = 0xffffffffu;
+    constexpr int W = HC / 32;
+    const int lane = threadIdx.x & 31;
+    HashTable<HC, ScanSmemBit<HC, NBK>> tab{&sm, A.limit};
+    int *rv = sm.val;
+    u32 *bits = sm.bits;
+    {
+        int s0 = lane == 0 ? tab.find(start) : 0;
+        s0 = __shfl_sync(kAll, s0, 0);
+        if (lane == 0) bits[s0 >> 5] |= 1u << (s0 & 31);  // key 0
+        __syncwarp();
+    }
+    int top = 0;  // keys above top are empty
+    auto search = [&]() -> unsigned {
+        for (; top >= 0; --top) {
+            const u32 w = lane < W ? bits[top * W + lane] : 0u;
+            const unsigned v = __reduce_min_sync(kAll, w ? (unsigned)(lane * 32 + __ffs(w) - 1) : kAll);
+            if (v != kAll) return ((unsigned)(top + 1) << 10) | (1023u - v);
+        }
+        top = 0;
+        return 0u;
+    };
+    long long alpha = 0;
+    // lambda-hat as of the scan's start, lowered by the scan's own alpha (as
+    // in scan_one); the scan's best alpha and its prefix go straight to the
+    // record (rare)
+    long long L = ld_volatile_i64(&A.st->lam);
+    int Lj = L <= C ? (int)L : INT_MAX;  // the join threshold: none above C
+    if (lane == 0) {
+        A.rec_alpha[sid] = LLONG_MAX;
+        A.rec_len[sid] = 0;
+    }
+    int nS = 0;
+    bool alpha_ok = true;
+    cnt.scans++;
+    unsigned pe = search();
+    // the candidate's slot (-2 - slot when another scan owned it) and row
+    int spec_s = -1, spec_a0 = 0, spec_a1 = 0;
+    while (pe != 0u) {
+        const int s = 1023 - (int)(pe & 1023u), Kp = (int)(pe >> 10) - 1;
+        const int x = tab.vertex(s);
+        const int rx = rv[s];
+        const bool hit = s == spec_s, owned = s == -2 - spec_s;
+        if (lane == 0) {
+            bits[Kp * W + (s >> 5)] &= ~(1u << (s & 31));
+            rv[s] = kDone;
+        }
+        int old = 0, revisit = 0, a0 = 0, a1 = 0;
+        long long dx = 0;
+        int2 e = make_int2(0, 0);
+        if (!MULTI && owned) {
+            old = 1;  // owned when looked up: blacklisted without a claim
+        } else {
+            if (hit || owned) {  // owned here: several visits, the claim decides
+                a0 = spec_a0;
+                a1 = spec_a1;
+                if (hit && a0 + lane < a1) e = A.g.adj[a0 + lane];  // with the claim
+            } else {
+                a0 = A.g.rp[x];
+                a1 = A.g.rp[x + 1];
+            }
+            if (lane == 0) {
+                dx = A.g.deg[x];
+                old = atomicCAS(&A.T[x], 0, sid);
+                // another scan owns x: one of its visits > 1 (Sec. 3.2)?
+                if (MULTI && old > 0) revisit = atomicAdd(&A.V[x], 1) < A.visits - 1;
+            }
+        }
+        __syncwarp();  // the pop's bit is cleared before the search
+        // the candidate before x's row is applied, its row offsets and owner
+        const unsigned qe = search();
+        spec_s = 1023 - (int)(qe & 1023u);
+        if (qe != 0u) {
+            const int vq = tab.vertex(spec_s);
+            spec_a0 = A.g.rp[vq];
+            spec_a1 = A.g.rp[vq + 1];
+            if (*(volatile int *)&A.T[vq] != 0) spec_s = -2 - spec_s;
+        } else {
+            spec_s = -1;
+        }
+        old = __shfl_sync(kAll, old, 0);
+        if (MULTI) revisit = __shfl_sync(kAll, revisit, 0);
+        if (old != 0 && !revisit) {
+            cnt.black++;
+            pe = qe;
+            continue;
+        }
+        // a vertex this scan does not own is not in its recorded prefix: its
+        // later alpha values could not be traced back to a side
+        if (MULTI && old != 0) alpha_ok = false;
+        if (lane == 0 && old == 0) A.order[x] = nS;
+        dx = __shfl_sync(kAll, dx, 0);
+        ++nS;
+        if (rx >= kSat) alpha_ok = false;
+        alpha += dx - 2LL * rx;
+        if (alpha_ok && nS < A.g.n && alpha < L) {
+            if (lane == 0) {
+                atomicMin(&A.st->lam, alpha);
+                A.rec_alpha[sid] = alpha;
+                A.rec_len[sid] = nS;
+            }
+            L = alpha;
+            Lj = L <= C ? (int)L : INT_MAX;
+        }
+        cnt.verts++;
+        cnt.arcs += a1 - a0;
+        unsigned be = qe;  // the next pop: the candidate or a larger move
+        int xh = x;        // the last root seen for x's set
+        for (int i0 = a0; i0 < a1; i0 += 32) {
+            const int i = i0 + lane;
+            const bool v = i < a1;
+            if (v && (i0 != a0 || !hit)) e = A.g.adj[i];
+            const int y = e.x;
+            const int s2 = v ? tab.find(y) : -1;
+            // a full table refuses new vertices: the arc stays unscanned (its
+            // weight is 0 in Lemma 1's lowered graph) and alpha is no longer
+            // the cut of S, but the scan goes on over the vertices it holds
+            if (__any_sync(kAll, v && s2 < 0)) alpha_ok = false;
+            bool join = false;
+            unsigned me = 0u;
+            if (s2 >= 0) {
+                const int ro = rv[s2];
+                if (ro != kDone) {
+                    const int rn = sat_add(ro, e.y);
+                    rv[s2] = rn;
+                    // a certificate q = min(r, C) can only vouch for bounds <= C
+                    join = ro < Lj && Lj <= rn;
+                    const int ko = ro == 0 ? -1 : (ro < C ? ro : C), kn = rn < C ? rn : C;
+                    if (ko != kn) {
+                        const u32 bit = 1u << (s2 & 31);
+                        if (ko >= 0) atomicAnd(&bits[ko * W + (s2 >> 5)], ~bit);
+                        atomicOr(&bits[kn * W + (s2 >> 5)], bit);
+                        me = ((unsigned)(kn + 1) << 10) | (unsigned)(1023 - s2);
+                    }
+                }
+            }
+            int rt = INT_MAX;
+            if (join && uf_union_root(A.par, xh, y, &rt)) cnt.unions++;
+            rt = __reduce_min_sync(kAll, rt);
+            if (rt != INT_MAX) xh = rt;
+            me = __reduce_max_sync(kAll, me);
+            be = me > be ? me : be;
+        }
+        const int kb = (int)(be >> 10) - 1;
+        top = kb > top ? kb : top;
+        pe = be;
+        __syncwarp();
+    }
+}
 
 template <int HC_, int NB_>
 struct SmemQ : BucketQ<unsigned short, NB_> {
