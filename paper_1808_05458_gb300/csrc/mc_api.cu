@@ -288,8 +288,7 @@ int lp_bound(mc_graph *g, const mc_options &o, i64 &lam, cudaStream_t s, bool ve
         // the learned proposer votes on the first level's clusters
         if (pp && level == 0) MC_TRY(proposer_on_clusters(g, *pp, cur, delta_cl, lam, verbose, s));
         // Padberg-Rinaldi on the cluster graph
-        MC_TRY(union_find_init(w.par, cur.n, s));
-        MC_TRY(round_reset(w, lam, s));
+        MC_TRY(round_start(w, cur.n, lam, s));
         MC_TRY(pr_tests_budget(cur, w, lam, 1, 4, 64, s));
         MC_TRY(status_read(w, s));
         if (w.h_st->unions > 0 && cur.n >= 2) {
@@ -414,8 +413,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
         }
         cfg.round = rounds + guard;
         i64 thr = threshold();
-        MC_TRY(union_find_init(w.par, cur.n, s));
-        MC_TRY(round_reset(w, thr, s));
+        MC_TRY(round_start(w, cur.n, thr, s));
         // PR1/PR2 and the degree-2 rule on the input graph pass nothing when
         // every weight is below lambda-hat and half of delta and no row has
         // two arcs (unit-weight graphs with delta >= 3): skipped there
@@ -514,6 +512,7 @@ int solve_impl(mc_graph *g, const mc_options &o, cudaStream_t s, SolveOut &out) 
             return min_degree(*nxt, w, s);
         }));
         if (w.h_st->err & kErrOverflow) return MC_EOVERFLOW;
+        if (w.h_st->err & kErrNoProgress) return MC_EINTERNAL;
         bytes += cur.arcs * 20 + w.last_emitted * 12 + (i64)cur.n * 16 + (i64)n0 * 8;
         if (nxt->n >= 2 && w.h_st->mindeg < lam) {
             lam = w.h_st->mindeg;
@@ -877,8 +876,7 @@ int mc_step_contract(mc_graph *g, const int32_t *lab, int32_t nc, int64_t clamp,
 int mc_step_pr(mc_graph *g, int64_t lam, int32_t level, int32_t *labels) {
     if (!g || !labels || level < 0 || level > 4) return MC_EINVAL;
     cudaStream_t s = g->stream;
-    MC_TRY(union_find_init(g->w.par, g->n0, s));
-    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(round_start(g->w, g->n0, lam, s));
     MC_TRY(pr_tests_budget(g->G0, g->w, lam, 1, level, -1, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_CUDA(cudaMemcpyAsync(labels, g->w.root, sizeof(int) * (size_t)g->n0, cudaMemcpyDeviceToHost, s));
@@ -899,8 +897,7 @@ int mc_step_capforest(mc_graph *g, int64_t lam, const mc_options *opt, int32_t *
     cfg.seed = o.seed;
     cfg.lam_hint = lam;
     cfg.visits = o.visits;
-    MC_TRY(union_find_init(g->w.par, g->n0, s));
-    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(round_start(g->w, g->n0, lam, s));
     MC_TRY(capforest_parallel(g->G0, g->w, cfg, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_TRY(status_read(g->w, s));
@@ -927,8 +924,7 @@ int mc_step_capforest_range(mc_graph *g, int64_t lam, const mc_options *opt, int
     cfg.visits = o.visits;
     cfg.lo = lo;
     cfg.hi = hi;
-    MC_TRY(union_find_init(w.par, g->n0, s));
-    MC_TRY(round_reset(w, lam, s));
+    MC_TRY(round_start(w, g->n0, lam, s));
     MC_TRY(capforest_parallel(g->G0, w, cfg, s));
     MC_TRY(flatten_labels(w, g->n0, s));
     MC_TRY(status_read(w, s));
@@ -956,8 +952,7 @@ int mc_step_capforest_full(mc_graph *g, int64_t lam, int32_t start, int32_t *lab
     ScanConfig cfg;
     cfg.start = start;
     cfg.lam_hint = lam;
-    MC_TRY(union_find_init(g->w.par, g->n0, s));
-    MC_TRY(round_reset(g->w, lam, s));
+    MC_TRY(round_start(g->w, g->n0, lam, s));
     MC_TRY(capforest_full(g->G0, g->w, cfg, s));
     MC_TRY(flatten_labels(g->w, g->n0, s));
     MC_TRY(status_read(g->w, s));

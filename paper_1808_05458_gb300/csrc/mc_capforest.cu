@@ -640,16 +640,29 @@ __global__ void k_apply_pairs(const u64 *__restrict__ pairs, Status *st, int *pa
 }
 
 // smallest scan id whose best alpha equals lambda-hat
-__global__ void k_best_scan(const i64 *__restrict__ rec_alpha, const int *__restrict__ rec_len, Status *st) {
+// the smallest scan id whose alpha equals the final lambda-hat, and that
+// scan's prefix length (read by the last block to finish; its block counter
+// `done` comes back to 0)
+__global__ void k_best_scan(const i64 *__restrict__ rec_alpha, const int *__restrict__ rec_len, Status *st,
+                            unsigned *done) {
+    __shared__ bool last;
     const int ns = st->scan_ids;
     const long long lam = st->lam;
     for (int s = 1 + blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += gridDim.x * blockDim.x)
         if (rec_alpha[s] == lam) atomicMin(&st->best_scan, s);
-}
-
-__global__ void k_best_len(const int *__restrict__ rec_len, Status *st) {
-    st->best_len = st->best_scan < INT_MAX ? rec_len[st->best_scan] : 0;
-    if (st->best_scan == INT_MAX) st->best_scan = -1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const int b = *(volatile int *)&st->best_scan;
+        st->best_len = b < INT_MAX ? rec_len[b] : 0;
+        if (b == INT_MAX) st->best_scan = -1;
+        *done = 0;
+    }
 }
 
 __global__ void k_scan_reset(Status *st) {
@@ -761,7 +774,13 @@ constexpr int kHubArcs = 4096;
 // owners start at 0 (free) or -1 (never scanned): hubs, and the vertices
 // outside [lo, hi) when a rank scans only the vertices it owns (Sec. 3.2:
 // a vertex passed over is a blacklisted one, Lemma 2 part 3)
-__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T, int *V, int lo, int hi) {
+__global__ void k_owner_init(const int *__restrict__ rp, int n, int *T, int *V, int lo, int hi, Status *st) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the scan status (k_scan_reset's fields)
+        st->cursor = 0;
+        st->scan_ids = 0;
+        st->best_scan = INT_MAX;
+        st->best_len = 0;
+    }
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         T[v] = (rp[v + 1] - rp[v] > kHubArcs || v < lo || v >= hi) ? -1 : 0;
         if (V) V[v] = 0;
@@ -777,9 +796,8 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
         // round uses while the scans run
         const int lo = cfg.lo > 0 ? cfg.lo : 0, hi = cfg.hi >= 0 && cfg.hi < g.n ? cfg.hi : g.n;
         ++::mc::g_launches;
-        k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T, cfg.visits > 1 ? w.cnt : nullptr, lo, hi);
+        k_owner_init<<<blocks, 256, 0, s>>>(g.rp, g.n, w.T, cfg.visits > 1 ? w.cnt : nullptr, lo, hi, w.st);
     }
-    ++::mc::g_launches; k_scan_reset<<<1, 1, 0, s>>>(w.st);
     ScanArgs A = make_args(g, w, cfg);
     A.visits = cfg.visits > 1 ? cfg.visits : 1;
     A.V = w.cnt;
@@ -820,8 +838,8 @@ int capforest_parallel(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaSt
         rc = launch_parallel<WPB, 2048, 256>(A, cfg.pq_fifo, cfg.warps, s);
     }
     if (rc != MC_OK) return rc;
-    ++::mc::g_launches; k_best_scan<<<64, 256, 0, s>>>(w.rec_alpha, w.rec_len, w.st);
-    ++::mc::g_launches; k_best_len<<<1, 1, 0, s>>>(w.rec_len, w.st);
+    ++::mc::g_launches;
+    k_best_scan<<<64, 256, 0, s>>>(w.rec_alpha, w.rec_len, w.st, reinterpret_cast<unsigned *>(w.red + kRedBestDone));
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
@@ -878,8 +896,8 @@ int capforest_full(const DevGraph &g, Work &w, const ScanConfig &cfg, cudaStream
         if (blocks < 1) blocks = 1;
         ++::mc::g_launches; k_apply_pairs<<<blocks, 256, 0, s>>>(w.keysA, w.st, w.par);
     }
-    ++::mc::g_launches; k_best_scan<<<1, 32, 0, s>>>(w.rec_alpha, w.rec_len, w.st);
-    ++::mc::g_launches; k_best_len<<<1, 1, 0, s>>>(w.rec_len, w.st);
+    ++::mc::g_launches;
+    k_best_scan<<<1, 32, 0, s>>>(w.rec_alpha, w.rec_len, w.st, reinterpret_cast<unsigned *>(w.red + kRedBestDone));
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }

@@ -54,7 +54,10 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
     MC_TRY(dev_alloc_n(&w.order, (size_t)n0, s));
     MC_TRY(dev_alloc_n(&w.cnt, (size_t)n0, s));
     MC_TRY(dev_alloc_n(&w.orig, (size_t)n0, s));
+    MC_TRY(dev_alloc_n(&w.red, (size_t)kRedWords, s));
+    MC_CUDA(cudaMemsetAsync(w.red, 0, sizeof(i64) * (size_t)kRedWords, s));
     MC_TRY(dev_alloc_n(&w.scan_tmp, scan_tmp_words(a * 256), s));
+    MC_TRY(scan_tmp_clear(w.scan_tmp, scan_tmp_words(a * 256), s));
     MC_TRY(dev_alloc_n(&w.keysA, (size_t)a, s));
     MC_TRY(dev_alloc_n(&w.keysB, (size_t)a, s));
     MC_TRY(dev_alloc_n(&w.valsA, (size_t)a, s));
@@ -71,7 +74,7 @@ int work_alloc(Work &w, i64 n0, i64 arcs0, cudaStream_t s) {
 }
 
 void work_free(Work &w, cudaStream_t s) {
-    void *ps[] = {w.par, w.root, w.lab, w.T, w.order, w.cnt, w.orig, w.scan_tmp, w.keysA, w.keysB,
+    void *ps[] = {w.par, w.root, w.lab, w.T, w.order, w.cnt, w.orig, w.red, w.scan_tmp, w.keysA, w.keysB,
                   w.valsA, w.valsB, w.radix_tmp, w.rec_alpha, w.rec_len, w.fb_r, w.fb_pool,
                   w.best_side, w.st, w.tail, w.blk};
     for (void *p : ps) dev_free(p, s);
@@ -94,7 +97,8 @@ int union_find_init(int *par, int n, cudaStream_t s) {
 // to their own array: a find's path-halving store into par[v] may land after
 // v's own root store and leave par[v] at a lower ancestor, so par is never
 // the output.
-__global__ void k_flatten(int *par, int *__restrict__ root, int *__restrict__ cnt, int n) {
+__global__ void k_flatten(int *par, int *__restrict__ root, int *__restrict__ cnt, int n, Status *st) {
+    if (st && blockIdx.x == 0 && threadIdx.x == 0) st->count2 = 0;  // the emit counter
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int r = uf_find(par, v);
         cnt[v] = (r == v);
@@ -355,36 +359,61 @@ __global__ void k_rowptr(const int *__restrict__ osrc, const int *d_m, int nc, i
 }
 
 // ------------------------------------------------------------ min degree --
-__global__ void k_min_deg(const i64 *__restrict__ deg, int n, Status *st) {
-    __shared__ long long red[kThreads / 32];
-    long long best = LLONG_MAX;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        best = min(best, deg[v]);
+// minimum weighted degree and the smallest vertex with it, in one launch:
+// each block reduces its vertices to (degree, vertex), and the last block to
+// finish reduces the blocks' pairs (its counter comes back to 0)
+__device__ __forceinline__ void md_better(long long &d, int &v, long long d2, int v2) {
+    if (d2 < d || (d2 == d && v2 < v)) { d = d2; v = v2; }
+}
+
+// thread 0 ends with the block's best pair
+__device__ void md_block_reduce(long long &d, int &v) {
+    __shared__ long long sd[kThreads / 32];
+    __shared__ int sv[kThreads / 32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    for (int o = 16; o > 0; o >>= 1)
+        md_better(d, v, __shfl_xor_sync(0xffffffffu, d, o), __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d; sv[threadIdx.x >> 5] = v; }
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < kThreads / 32; ++k) md_better(d, v, sd[k], sv[k]);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_min_deg(const i64 *__restrict__ deg, int n, Status *st, long long *part, unsigned *done) {
+    __shared__ bool last;
+    long long d = LLONG_MAX;
+    int v = INT_MAX;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        md_better(d, v, deg[u], u);
+    md_block_reduce(d, v);
     if (threadIdx.x == 0) {
-        for (int k = 1; k < kThreads / 32; ++k) best = min(best, red[k]);
-        atomicMin(&st->mindeg, best);
+        part[2 * blockIdx.x] = d;
+        part[2 * blockIdx.x + 1] = v;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    d = LLONG_MAX;
+    v = INT_MAX;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        md_better(d, v, *(volatile long long *)&part[2 * b], (int)*(volatile long long *)&part[2 * b + 1]);
+    md_block_reduce(d, v);
+    if (threadIdx.x == 0) {
+        st->mindeg = d;
+        st->argmin = v;
+        *done = 0;
     }
 }
 
-__global__ void k_argmin_deg(const i64 *__restrict__ deg, int n, Status *st) {
-    const long long md = st->mindeg;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        if (deg[v] == md) atomicMin(&st->argmin, v);
-}
-
-__global__ void k_reset_min(Status *st) {
-    st->mindeg = LLONG_MAX;
-    st->argmin = INT_MAX;
-}
-
 int min_degree(const DevGraph &g, Work &w, cudaStream_t s) {
-    ++::mc::g_launches; k_reset_min<<<1, 1, 0, s>>>(w.st);
-    ++::mc::g_launches; k_min_deg<<<grid_for(g.n), kThreads, 0, s>>>(g.deg, g.n, w.st);
-    ++::mc::g_launches; k_argmin_deg<<<grid_for(g.n), kThreads, 0, s>>>(g.deg, g.n, w.st);
+    int blocks = grid_for(g.n);
+    if (blocks > kMinDegBlocks) blocks = kMinDegBlocks;
+    ++::mc::g_launches;
+    k_min_deg<<<blocks, kThreads, 0, s>>>(g.deg, g.n, w.st, w.red, reinterpret_cast<unsigned *>(w.red + kRedMinDone));
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
@@ -435,7 +464,7 @@ static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cu
                             const std::function<int()> &post) {
     bool in_b = false;
     MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, m, bits_for((u64)nc * (u64)nc - 1),
-                            w.radix_tmp, w.scan_tmp, &in_b, s));
+                            w.radix_tmp, w.scan_tmp, &w.st->err, &in_b, s));
     u64 *keys = in_b ? w.keysB : w.keysA;
     int *vals = in_b ? w.valsB : w.valsA;
     int *flags = in_b ? w.valsA : w.valsB;      // free int32 buffer
@@ -445,7 +474,7 @@ static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cu
     MC_CUDA(cudaMemsetAsync(out.deg, 0, sizeof(i64) * (size_t)nc, s));
     if (m > 0) {
         ++::mc::g_launches; k_heads<<<grid_for(m), kThreads, 0, s>>>(keys, m, flags);
-        MC_TRY(exclusive_scan_i32(flags, flags, m, d_total, w.scan_tmp, s));
+        MC_TRY(exclusive_scan_i32(flags, flags, m, d_total, w.scan_tmp, &w.st->err, s));
         MC_CUDA(cudaMemsetAsync(acc, 0, sizeof(u64) * (size_t)m, s));
         ++::mc::g_launches; k_seg_sum<<<grid_for(m), kThreads, 0, s>>>(keys, vals, flags, m, (u64)nc, acc, out.src,
                                                    out.adj);
@@ -465,12 +494,13 @@ static int build_from_pairs(i64 m, int nc, i64 clamp, DevGraph &out, Work &w, cu
 int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool flatten, int nc,
                    cudaStream_t s, const std::function<int()> &post) {
     const int n = in.n;
-    ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
+    // count2 (the emitted arcs) starts at 0: zeroed by the flatten, else here
+    if (!flatten) { ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st); }
     const int *d_nc = nullptr;
     if (flatten) {
-        ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n);
+        ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n, w.st);
         d_nc = reinterpret_cast<int *>(&w.st->count);
-        MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
+        MC_TRY(exclusive_scan_i32(w.cnt, w.lab, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, &w.st->err, s));
         ++::mc::g_launches; k_relabel<<<grid_for(n), kThreads, 0, s>>>(w.root, w.lab, n);
     }
     // block count (device) and emitted arcs in one status read
@@ -596,6 +626,7 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     }
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err & kErrOverflow) return MC_EOVERFLOW;
+    if (wk.h_st->err & kErrNoProgress) return MC_EINTERNAL;
     if (wk.h_st->err) return MC_EINVAL;
     if (check_sym && wk.h_st->count != wk.h_st->count2) return MC_EINVAL;
     return MC_OK;
@@ -659,13 +690,13 @@ int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s)
     if (g.arcs > 0) {
         int *giant = reinterpret_cast<int *>(&w.st->count2);
         ++::mc::g_launches; k_cc_sample<<<grid_for((i64)g.n * kCcSample), kThreads, 0, s>>>(g, w.par);
-        ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n);
+        ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n, nullptr);
         ++::mc::g_launches; k_cc_giant<<<1, kCcProbe, 0, s>>>(w.root, g.n, giant);
         ++::mc::g_launches; k_cc_finish<<<grid_for((i64)g.n * 32), kThreads, 0, s>>>(g, w.root, giant, w.par);
     }
-    ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n);
+    ++::mc::g_launches; k_flatten<<<grid_for(g.n), kThreads, 0, s>>>(w.par, w.root, w.cnt, g.n, nullptr);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
-    MC_TRY(exclusive_scan_i32(w.cnt, w.lab, g.n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
+    MC_TRY(exclusive_scan_i32(w.cnt, w.lab, g.n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, &w.st->err, s));
     MC_TRY(status_read(w, s));
     *ncomp = (int)w.h_st->count;
     return MC_OK;
@@ -739,12 +770,12 @@ int orig_update(Work &w, int n0, cudaStream_t s) {
 namespace mc {
 
 int flatten_labels(Work &w, int n, cudaStream_t s) {
-    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n);
+    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(w.par, w.root, w.cnt, n, nullptr);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
 
-__global__ void k_round_reset(Status *st, long long lam) {
+__device__ __forceinline__ void round_reset_body(Status *st, long long lam) {
     st->lam = lam;
     st->unions = 0;
     st->scanned_arcs = 0;
@@ -752,6 +783,20 @@ __global__ void k_round_reset(Status *st, long long lam) {
     st->scans = 0;
     st->blacklisted = 0;
     st->err = 0;
+}
+
+__global__ void k_round_reset(Status *st, long long lam) { round_reset_body(st, lam); }
+
+// union_find_init and round_reset in one launch
+__global__ void k_round_start(int *par, int n, Status *st, long long lam) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) round_reset_body(st, lam);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) par[v] = v;
+}
+
+int round_start(Work &w, int n, i64 lam, cudaStream_t s) {
+    ++::mc::g_launches; k_round_start<<<grid_for(n), kThreads, 0, s>>>(w.par, n, w.st, lam);
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
 }
 
 int round_reset(Work &w, i64 lam, cudaStream_t s) {
@@ -789,7 +834,7 @@ int iota_i32(int *a, int n, cudaStream_t s) {
 
 // flatten a caller-provided union-find array: root[v] = root of v
 int flatten_raw(int *par, int *root, int *cnt, int n, cudaStream_t s) {
-    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(par, root, cnt, n);
+    ++::mc::g_launches; k_flatten<<<grid_for(n), kThreads, 0, s>>>(par, root, cnt, n, nullptr);
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
@@ -810,7 +855,7 @@ int compact_labels(Work &w, int n, int *nc, cudaStream_t s) {
     ++::mc::g_launches; k_mark_used<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.root, n);
     ++::mc::g_launches; k_mark_used2<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.root, n);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(w.st);
-    MC_TRY(exclusive_scan_i32(w.root, w.par, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, s));
+    MC_TRY(exclusive_scan_i32(w.root, w.par, n, reinterpret_cast<int *>(&w.st->count), w.scan_tmp, &w.st->err, s));
     ++::mc::g_launches; k_apply_ids<<<grid_for(n), kThreads, 0, s>>>(w.lab, w.par, n);
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(w, s));

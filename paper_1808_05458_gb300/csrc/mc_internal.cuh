@@ -101,10 +101,13 @@ constexpr int kErrNoProgress = 16;
 // --------------------------------------------------------------- launches --
 int num_sms();
 
-// device-wide exclusive scan of int32 counts into int32 offsets; *d_total
-// receives the sum (may be nullptr).  tmp must hold scan_tmp_words(n) ints.
+// device-wide exclusive scan of int32 counts into int32 offsets (one launch
+// up to 2^19 items, two beyond); *d_total receives the sum (may be nullptr).
+// tmp must hold scan_tmp_words(n) ints, cleared whole once by scan_tmp_clear,
+// and serve one stream; a stuck wait sets kErrNoProgress in *err.
 size_t scan_tmp_words(i64 n);
-int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp,
+int scan_tmp_clear(int *tmp, size_t words, cudaStream_t s);
+int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp, int *err,
                        cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs on the low `bits` bits of the keys.
@@ -112,9 +115,14 @@ int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tm
 // tmp must hold radix_tmp_words(n) uint32.
 size_t radix_tmp_words(i64 n);
 int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int bits,
-                     u32 *tmp, int *scan_tmp, bool *in_b, cudaStream_t s);
+                     u32 *tmp, int *scan_tmp, int *err, bool *in_b, cudaStream_t s);
 
 // Contraction workspace.
+constexpr int kMinDegBlocks = 1024;  // blocks of one min_degree launch at most
+constexpr int kRedMinDone = 2 * kMinDegBlocks;
+constexpr int kRedBestDone = 2 * kMinDegBlocks + 1;
+constexpr int kRedWords = 2 * kMinDegBlocks + 2;
+
 struct Work {
     // per-vertex (sized n0)
     int *par = nullptr;      // union-find parents
@@ -125,6 +133,9 @@ struct Work {
     int *cnt = nullptr;      // per-vertex counts / flags
     int *orig = nullptr;     // original vertex -> current vertex
     int *scan_tmp = nullptr;
+    // min_degree's per-block pairs and block counter, the best-scan search's
+    // block counter (kRed* below)
+    i64 *red = nullptr;
     // per-arc (sized arcs0)
     u64 *keysA = nullptr, *keysB = nullptr;
     int *valsA = nullptr, *valsB = nullptr;
@@ -214,6 +225,7 @@ int pr_tests_budget(const DevGraph &g, Work &w, i64 lam, int lo, int level, int 
                     cudaStream_t s);
 int flatten_labels(Work &w, int n, cudaStream_t s);   // w.root[v] = root of v in w.par
 int round_reset(Work &w, i64 lam, cudaStream_t s);    // st->lam = lam, counters = 0
+int round_start(Work &w, int n, i64 lam, cudaStream_t s);  // union_find_init + round_reset
 int side_canon(Work &w, int n0, cudaStream_t s);
 int iota_i32(int *a, int n, cudaStream_t s);
 const std::string &error_detail();

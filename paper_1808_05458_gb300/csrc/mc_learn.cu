@@ -860,7 +860,7 @@ int proposer_sweep(Proposer &p, const DevGraph &g, Work &w, long long *cut, int 
     const int tb = blocks_for(n, 256);
     ++::mc::g_launches; k_score_keys<<<tb, 256, 0, s>>>(p.S, n, w.keysA, w.valsA);
     bool in_b = false;
-    MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, n, 32, w.radix_tmp, w.scan_tmp, &in_b, s));
+    MC_TRY(radix_sort_pairs(w.keysA, w.valsA, w.keysB, w.valsB, n, 32, w.radix_tmp, w.scan_tmp, &w.st->err, &in_b, s));
     const int *order = in_b ? w.valsB : w.valsA;
     ++::mc::g_launches; k_rank<<<tb, 256, 0, s>>>(order, n, w.root);
     long long *term = reinterpret_cast<long long *>(in_b ? w.keysA : w.keysB);

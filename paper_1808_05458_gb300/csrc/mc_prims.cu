@@ -123,70 +123,222 @@ __device__ __forceinline__ T block_excl_scan(T v, T *total) {
     return r;
 }
 
-__global__ void k_tile_reduce(const int *__restrict__ in, i64 n, int *__restrict__ part) {
-    i64 base = (i64)blockIdx.x * kScanTile;
+// Single-pass exclusive scan with decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), for up
+// to kScanLookTiles tiles: each block takes the next tile index from a
+// counter (so every tile it waits on belongs to a block that started before
+// it), publishes its tile's sum, then reads its predecessors' published
+// words, 32 * kScanLook per round trip, adding sums back to the nearest
+// published prefix, and publishes its own prefix.
+//
+// tmp: a header {tile counter, finished blocks, epoch, -} and one 64-bit word
+// per tile, (epoch << 34) | (state << 32) | value with state 1 = the tile's
+// sum, 2 = its inclusive prefix; a word of another epoch is unpublished.  The
+// last block to finish resets the counters and advances the epoch, so the
+// buffer needs no clearing between calls (stream-ordered calls only).  A wait
+// that outlasts kScanSpinLimit polls sets kErrNoProgress in *err and takes 0
+// for the rest (it cannot happen while blocks start in tile order).
+constexpr long long kScanSpinLimit = 1LL << 22;
+constexpr int kScanLook = 8;        // predecessor words per lane and round trip
+constexpr int kScanLookTiles = 256;  // larger inputs take the two-launch path
+
+struct ScanHeader {
+    unsigned tiles, done, epoch, large_done;
+};
+
+__device__ __forceinline__ u64 scan_word(unsigned epoch, unsigned state, unsigned v) {
+    return ((u64)(epoch & 0x3FFFFFFFu) << 34) | ((u64)state << 32) | v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan1(const int *in, int *out, i64 n, int *d_total, unsigned *tmp, int nt, int *err) {
+    ScanHeader *hdr = reinterpret_cast<ScanHeader *>(tmp);
+    u64 *words = reinterpret_cast<u64 *>(tmp + 4);
+    __shared__ int s_tile, s_prefix, s_tot;
+    __shared__ unsigned s_epoch;
+    if (threadIdx.x == 0) {
+        s_epoch = *(volatile unsigned *)&hdr->epoch;
+        s_tile = (int)atomicAdd(&hdr->tiles, 1u);
+    }
+    __syncthreads();
+    const int t = s_tile;
+    const unsigned ep = s_epoch & 0x3FFFFFFFu;
+    // blocked arrangement: thread k owns items [k*ITEMS, k*ITEMS+ITEMS)
+    const i64 base = (i64)t * kScanTile + (i64)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const i64 i = base + k;
+        v[k] = i < n ? in[i] : 0;
+        sum += v[k];
+    }
+    int ex = block_excl_scan<int, kScanThreads>(sum, &s_tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int agg = s_tot;
+        if (lane == 0) *(volatile u64 *)&words[t] = scan_word(ep, t == 0 ? 2u : 1u, (unsigned)agg);
+        int excl = 0;
+        long long spins = 0;
+        for (int j = t - 1; j >= 0;) {
+            // lane l reads tiles j - l - 32k; below tile 0: a prefix of 0
+            unsigned st[kScanLook], val[kScanLook];
+#pragma unroll
+            for (int k = 0; k < kScanLook; ++k) {
+                const int idx = j - lane - 32 * k;
+                st[k] = 2u;
+                val[k] = 0u;
+                if (idx >= 0) {
+                    const u64 w = *(volatile u64 *)&words[idx];
+                    st[k] = (unsigned)(w >> 34) == ep ? (unsigned)(w >> 32) & 3u : 0u;
+                    val[k] = (unsigned)w;
+                }
+            }
+            // the nearest prefix P in the window (-1: tile 0's virtual
+            // predecessor, -2: none); the walk ends at P once every tile after
+            // it has published
+            int near = -2;
+#pragma unroll
+            for (int k = 0; k < kScanLook; ++k) {
+                const int idx = j - lane - 32 * k;
+                const int at = idx >= 0 ? idx : -1;
+                if (st[k] == 2u && at > near) near = at;
+            }
+            const int P = __reduce_max_sync(0xffffffffu, near);
+            bool waiting = false;
+            unsigned part = 0;
+#pragma unroll
+            for (int k = 0; k < kScanLook; ++k) {
+                const int idx = j - lane - 32 * k;
+                if (idx >= P) {
+                    waiting |= st[k] == 0u;
+                    part += val[k];
+                }
+            }
+            if (__any_sync(0xffffffffu, waiting)) {
+                if (++spins > kScanSpinLimit) {
+                    if (lane == 0) atomicOr(err, kErrNoProgress);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += (int)__reduce_add_sync(0xffffffffu, part);
+            if (P >= -1) break;
+            j -= 32 * kScanLook;
+        }
+        if (lane == 0) {
+            if (t > 0) *(volatile u64 *)&words[t] = scan_word(ep, 2u, (unsigned)(excl + agg));
+            s_prefix = excl;
+            if (t == nt - 1 && d_total) *d_total = excl + agg;
+        }
+    }
+    __syncthreads();
+    ex += s_prefix;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const i64 i = base + k;
+        if (i < n) out[i] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0 && atomicAdd(&hdr->done, 1u) == (unsigned)nt - 1u) {
+        // every block took its tile and finished: reset for the next call
+        hdr->tiles = 0;
+        hdr->done = 0;
+        hdr->epoch = hdr->epoch + 1u;
+    }
+}
+
+// Larger inputs: the look-back walk grows with the tile count, so two
+// launches instead -- each tile's sum, the last block to finish scanning the
+// sums (its counter comes back to 0), then each tile's scan from its offset.
+__global__ void __launch_bounds__(kScanThreads)
+k_tile_reduce(const int *__restrict__ in, i64 n, int *part, int nt, int *d_total, unsigned *done) {
+    __shared__ int tot;
+    __shared__ bool last;
+    const i64 base = (i64)blockIdx.x * kScanTile;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        i64 i = base + (i64)k * kScanThreads + threadIdx.x;
+        const i64 i = base + (i64)k * kScanThreads + threadIdx.x;
         if (i < n) s += in[i];
     }
-    __shared__ int tot;
-    int ex = block_excl_scan<int, kScanThreads>(s, &tot);
-    (void)ex;
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-// single block: exclusive scan of part[0..nt) in place, total to *d_total
-__global__ void k_scan_parts(int *part, int nt, int *d_total) {
-    const int per = (nt + 1023) / 1024;
-    int lo = threadIdx.x * per, hi = min(nt, lo + per);
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += part[i];
-    __shared__ int tot;
-    int ex = block_excl_scan<int, 1024>(s, &tot);
+    (void)block_excl_scan<int, kScanThreads>(s, &tot);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        __threadfence();
+        last = atomicAdd(done, 1u) == (unsigned)nt - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the tile sums, scanned in place by this block (a run per thread)
+    const int per = (nt + kScanThreads - 1) / kScanThreads;
+    const int lo = threadIdx.x * per, hi = min(nt, lo + per);
+    int r = 0;
+    for (int i = lo; i < hi; ++i) r += *(volatile int *)&part[i];
+    int ex = block_excl_scan<int, kScanThreads>(r, &tot);
     for (int i = lo; i < hi; ++i) {
-        int v = part[i];
+        const int v = *(volatile int *)&part[i];
         part[i] = ex;
         ex += v;
     }
-    if (threadIdx.x == 0 && d_total) *d_total = tot;
+    if (threadIdx.x == 0) {
+        if (d_total) *d_total = tot;
+        *done = 0;
+    }
 }
 
-__global__ void k_tile_scan(const int *__restrict__ in, int *__restrict__ out, i64 n,
-                            const int *__restrict__ part) {
-    // blocked arrangement: thread t owns items [t*ITEMS, t*ITEMS+ITEMS)
-    i64 base = (i64)blockIdx.x * kScanTile + (i64)threadIdx.x * kScanItems;
+__global__ void __launch_bounds__(kScanThreads)
+k_tile_scan(const int *__restrict__ in, int *__restrict__ out, i64 n, const int *__restrict__ part) {
+    __shared__ int tot;
+    const i64 base = (i64)blockIdx.x * kScanTile + (i64)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        i64 i = base + k;
+        const i64 i = base + k;
         v[k] = i < n ? in[i] : 0;
         s += v[k];
     }
-    __shared__ int tot;
     int ex = block_excl_scan<int, kScanThreads>(s, &tot) + part[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        i64 i = base + k;
+        const i64 i = base + k;
         if (i < n) out[i] = ex;
         ex += v[k];
     }
 }
 
-size_t scan_tmp_words(i64 n) { return (size_t)div_up(n > 0 ? n : 1, kScanTile) + 32; }
+// tmp: the header {tile counter, finished blocks, epoch, two-launch block
+// counter}, the look-back words (2 ints per tile, at most kScanLookTiles
+// tiles), then the two-launch path's tile sums (1 int per tile)
+constexpr int kScanParts = 4 + 2 * kScanLookTiles;
+size_t scan_tmp_words(i64 n) { return kScanParts + (size_t)div_up(n > 0 ? n : 1, kScanTile) + 32; }
 
-int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp,
+int scan_tmp_clear(int *tmp, size_t words, cudaStream_t s) {
+    // the look-back words too: recycled memory may hold another buffer's
+    // words of the same epoch
+    MC_CUDA(cudaMemsetAsync(tmp, 0, words * sizeof(int), s));
+    return MC_OK;
+}
+
+int exclusive_scan_i32(const int *d_in, int *d_out, i64 n, int *d_total, int *tmp, int *err,
                        cudaStream_t s) {
     if (n <= 0) {
         if (d_total) MC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int), s));
         return MC_OK;
     }
-    int nt = div_up(n, kScanTile);
-    ++::mc::g_launches; k_tile_reduce<<<nt, kScanThreads, 0, s>>>(d_in, n, tmp);
-    ++::mc::g_launches; k_scan_parts<<<1, 1024, 0, s>>>(tmp, nt, d_total);
-    ++::mc::g_launches; k_tile_scan<<<nt, kScanThreads, 0, s>>>(d_in, d_out, n, tmp);
+    const int nt = div_up(n, kScanTile);
+    if (nt <= kScanLookTiles) {
+        ++::mc::g_launches;
+        k_scan1<<<nt, kScanThreads, 0, s>>>(d_in, d_out, n, d_total, reinterpret_cast<unsigned *>(tmp), nt, err);
+    } else {
+        int *part = tmp + kScanParts;
+        unsigned *done = reinterpret_cast<unsigned *>(tmp + 3);
+        ++::mc::g_launches; k_tile_reduce<<<nt, kScanThreads, 0, s>>>(d_in, n, part, nt, d_total, done);
+        ++::mc::g_launches; k_tile_scan<<<nt, kScanThreads, 0, s>>>(d_in, d_out, n, part);
+    }
     MC_CUDA(cudaGetLastError());
     return MC_OK;
 }
@@ -290,7 +442,7 @@ k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__re
 size_t radix_tmp_words(i64 n) { return (size_t)256 * div_up(n > 0 ? n : 1, kRsTile) + 64; }
 
 int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int bits, u32 *tmp,
-                     int *scan_tmp, bool *in_b, cudaStream_t s) {
+                     int *scan_tmp, int *err, bool *in_b, cudaStream_t s) {
     *in_b = false;
     if (n <= 1 || bits <= 0) return MC_OK;
     const int ntiles = div_up(n, kRsTile);
@@ -299,7 +451,7 @@ int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int 
     int *vi = valsA, *vo = valsB;
     for (int shift = 0; shift < bits; shift += 8) {
         ++::mc::g_launches; k_rs_hist<<<ntiles, kRsThreads, 0, s>>>(ki, n, shift, ntiles, hist);
-        MC_TRY(exclusive_scan_i32(hist, hist, (i64)256 * ntiles, nullptr, scan_tmp, s));
+        MC_TRY(exclusive_scan_i32(hist, hist, (i64)256 * ntiles, nullptr, scan_tmp, err, s));
         ++::mc::g_launches; k_rs_scatter<<<ntiles, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, hist);
         MC_CUDA(cudaGetLastError());
         u64 *tk = ki; ki = ko; ko = tk;

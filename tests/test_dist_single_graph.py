@@ -147,10 +147,14 @@ def _worker(rank, world, port, use_gpu, q):
         else:
             ops, small = CpuOps(), 2
         res = []
-        for g in (_graphs() if not use_gpu else _gpu_graphs()):
-            n, rp, col, w = _split(g, rank, world)
-            lam, side = sg.min_cut(comm, n, rp, col, w, ops=ops, small=small)
-            res.append((int(lam), side))
+        try:
+            for g in (_graphs() if not use_gpu else _gpu_graphs()):
+                n, rp, col, w = _split(g, rank, world)
+                lam, side = sg.min_cut(comm, n, rp, col, w, ops=ops, small=small)
+                res.append((int(lam), side))
+        except Exception as e:  # report at once instead of leaving the parent waiting
+            q.put((rank, repr(e)))
+            raise
         q.put((rank, res))
     finally:
         dist.destroy_process_group()
@@ -164,7 +168,11 @@ def _run(world, use_gpu=False, graphs=None):
     procs = [ctx.Process(target=_worker, args=(r, world, port, use_gpu, q)) for r in range(world)]
     for p in procs:
         p.start()
-    out = dict(q.get(timeout=600) for _ in range(world))
+    out = {}
+    for _ in range(world):
+        r, res = q.get(timeout=600)
+        assert not isinstance(res, str), f"rank {r}: {res}"
+        out[r] = res
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
