@@ -222,6 +222,8 @@ struct ScanArgs {
     // per-vertex count of the extra ones
     int visits = 1;
     int *V = nullptr;
+    // start candidates a warp takes from the shared cursor at a time
+    int grab = 32;
 };
 
 // per-warp totals of one launch (each is at most the graph's arc count, < 2^31)
