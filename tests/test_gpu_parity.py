@@ -666,7 +666,11 @@ def test_batch_asymmetric_rejected(mc):
     rp_m = np.array([0, 1, 2, 2], dtype=np.int32)   # 0 -> 1 and 1 -> 2 without mirrors
     col_m = np.array([1, 2], dtype=np.int32)
     w_m = np.array([1, 1], dtype=np.int32)
-    for bad in ((rp, col, w_bad), (rp_m, col_m, w_m)):
+    # every upward arc has its mirror, but the downward arc 2 -> 0 has none
+    # (as many arcs down as up fails)
+    g_down = (np.array([0, 1, 2, 3], dtype=np.int32), np.array([1, 0, 0], dtype=np.int32),
+              np.array([1, 1, 1], dtype=np.int32))
+    for bad in ((rp, col, w_bad), (rp_m, col_m, w_m), g_down):
         for graphs in ([bad], [good, bad, good]):
             with pytest.raises(mc.MinCutError) as ei:
                 mc.batch_min_cut(*_concat(graphs))
