@@ -15,10 +15,12 @@
 // gathers up to kLpBatch / 32 arcs of a batch at once -- all of their
 // {neighbour, weight} loads issued together, then all of their label loads
 // -- and adds each arc's weight into a per-warp shared-memory hash keyed by
-// (row, label).  Each row's choice comes from two passes over the table: the
-// largest total weight (32-bit shared atomics while every total fits in 31
-// bits, else one lane compares them all), then the smallest label reaching
-// it.  Longer rows
+// (row, label).  Each row's choice comes from one pass over the table with
+// 32-bit entries (a 64-bit atomicMax of total << 27 | (2^27 - 1 - label) per
+// row: the largest total, ties to the smallest label), or, with 64-bit
+// entries, two: the largest total weight (32-bit shared atomics while every
+// total fits in 31 bits, else one lane compares them all), then the smallest
+// label reaching it.  Longer rows
 // go to a block-per-vertex kernel with a global-memory hash slice of
 // 2^k > deg slots.
 #include "mc_internal.cuh"
@@ -27,13 +29,12 @@ namespace mc {
 
 namespace {
 
-constexpr int kLpWarps = 4;         // warps per block (35 KB of shared memory)
+constexpr int kLpWarps = 4;         // warps per block (19 KB of shared memory, 35 KB with 64-bit entries)
 constexpr int kLpRow = 256;         // longest row handled by the warp kernel
 constexpr int kLpBatch = 256;       // arcs per batch (whole rows)
 constexpr int kLpPer = kLpBatch / 32;
 constexpr int kLpHash = 512;        // per-warp hash slots (load <= 1/2)
 constexpr int kLpBigThreads = 256;
-constexpr unsigned long long kLpEmpty = ~0ULL;
 
 __device__ __forceinline__ int lp_parity(u64 seed, int sweep, int v) {
     return (int)(splitmix64(seed ^ splitmix64(((u64)(unsigned)sweep << 32) | (u64)(unsigned)v)) & 1ULL);
@@ -53,29 +54,59 @@ __device__ __forceinline__ void warp_argmax(long long &w, int &l) {
     }
 }
 
-struct LpSmem {
-    unsigned long long key[kLpHash];  // (row << 32) | label, or kLpEmpty
-    unsigned long long val[kLpHash];  // summed arc weight
-    unsigned bw[32];                  // per row: largest total weight (31-bit totals)
-    long long wide_w[32];             // per row: the same, when a total needs more bits
-    int bl[32];                       // per row: smallest label with it
-    int end[32];                      // per row: end of its arcs, laid end to end
-    int a0[32];                       // per row: its first arc
+// hash entries: (row << 32 | label, 64-bit total), or, when every label is
+// below 2^27 and every total below 2^31 (each weighted degree is), a 32-bit
+// key (row << 27 | label) and a 32-bit total: half the shared memory and
+// 32-bit atomics
+template <bool NARROW>
+struct LpT {
+    using K = unsigned long long;
+    using V = unsigned long long;
+    static constexpr K kEmpty = ~0ULL;
+    __device__ static K key(int row, int lab) { return ((K)row << 32) | (unsigned)lab; }
+    __device__ static int row(K k) { return (int)(k >> 32); }
+    __device__ static int lab(K k) { return (int)(unsigned)k; }
+    __device__ static unsigned slot(K k) {
+        const unsigned x = (unsigned)k * 2654435761u ^ (unsigned)(k >> 32) * 0x85EBCA6Bu;
+        return x >> (32 - 9);
+    }
+};
+template <>
+struct LpT<true> {
+    using K = unsigned;
+    using V = unsigned;
+    static constexpr K kEmpty = 0xFFFFFFFFu;
+    __device__ static K key(int row, int lab) { return ((unsigned)row << 27) | (unsigned)lab; }
+    __device__ static int row(K k) { return (int)(k >> 27); }
+    __device__ static int lab(K k) { return (int)(k & ((1u << 27) - 1u)); }
+    __device__ static unsigned slot(K k) { return (k * 2654435761u) >> (32 - 9); }
 };
 
-__device__ __forceinline__ unsigned lp_slot(unsigned long long key) {
-    const unsigned x = (unsigned)key * 2654435761u ^ (unsigned)(key >> 32) * 0x85EBCA6Bu;
-    return x >> (32 - 9);
-}
+template <bool NARROW>
+struct LpSmem {
+    typename LpT<NARROW>::K key[kLpHash];  // see LpT, or kEmpty
+    typename LpT<NARROW>::V val[kLpHash];  // summed arc weight
+    unsigned long long best[32];           // per row (32-bit entries): packed total and label
+    unsigned bw[32];                       // per row: largest total weight (31-bit totals)
+    long long wide_w[32];                  // per row: the same, when a total needs more bits
+    int bl[32];                            // per row: smallest label with it
+    int end[32];                           // per row: end of its arcs, laid end to end
+    int a0[32];                            // per row: its first arc
+};
 
+template <bool NARROW>
 __global__ void __launch_bounds__(kLpWarps * 32)
 k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const int *__restrict__ lin,
           int *__restrict__ lout, u64 seed, int sweep, int half, int *big_list, int *big_count) {
-    static_assert(kLpHash == 512, "lp_slot takes 9 bits");
-    __shared__ LpSmem sm[kLpWarps];
-    LpSmem &h = sm[threadIdx.x >> 5];
+    static_assert(kLpHash == 512, "the slot takes 9 bits");
+    using T = LpT<NARROW>;
+    using K = typename T::K;
+    using V = typename T::V;
+    __shared__ LpSmem<NARROW> sm[kLpWarps];
+    LpSmem<NARROW> &h = sm[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < kLpHash; i += 32) { h.key[i] = kLpEmpty; h.val[i] = 0; }
+    for (int i = lane; i < kLpHash; i += 32) { h.key[i] = T::kEmpty; h.val[i] = 0; }
+    h.best[lane] = 0;
     h.bw[lane] = 0;
     h.wide_w[lane] = -1;
     h.bl[lane] = INT_MAX;
@@ -147,39 +178,61 @@ k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const
 #pragma unroll
             for (int k = 0; k < kLpPer; ++k) {
                 if (row[k] < 0) continue;
-                const unsigned long long key = ((unsigned long long)row[k] << 32) | (unsigned)lab[k];
-                unsigned sl = lp_slot(key);
+                const K key = T::key(row[k], lab[k]);
+                unsigned sl = T::slot(key);
                 while (true) {
-                    const unsigned long long old = atomicCAS(&h.key[sl], kLpEmpty, key);
-                    if (old == kLpEmpty || old == key) break;
+                    const K old = atomicCAS(&h.key[sl], T::kEmpty, key);
+                    if (old == T::kEmpty || old == key) break;
                     sl = (sl + 1) & (kLpHash - 1);
                 }
-                atomicAdd(&h.val[sl], (unsigned long long)ed[k].y);
+                atomicAdd(&h.val[sl], (V)ed[k].y);
             }
             __syncwarp();
+            if constexpr (NARROW) {
+                // one pass: per row the largest (total, smallest label) as a
+                // 58-bit word (total << 27 | (2^27 - 1 - label)) by a shared
+                // 64-bit atomicMax; empty the table
+                for (int i = lane; i < kLpHash; i += 32) {
+                    const K key = h.key[i];
+                    if (key != T::kEmpty) {
+                        const unsigned long long pk =
+                            ((unsigned long long)h.val[i] << 27) | (unsigned)((1 << 27) - 1 - T::lab(key));
+                        atomicMax(&h.best[T::row(key)], pk);
+                        h.key[i] = T::kEmpty;
+                        h.val[i] = 0;
+                    }
+                }
+                __syncwarp();
+                if ((in_b >> lane) & 1u) {
+                    lout[v] = (1 << 27) - 1 - (int)(h.best[lane] & ((1u << 27) - 1u));
+                    h.best[lane] = 0;
+                }
+                __syncwarp();
+                continue;
+            }
             // pass 1: each row's largest total weight, by 32-bit atomics while
             // every total fits in 31 bits (else one lane compares them all)
             bool wide = false;
             for (int i = lane; i < kLpHash; i += 32) {
-                const unsigned long long key = h.key[i];
-                if (key == kLpEmpty) continue;
-                const unsigned long long t = h.val[i];
-                if (t >> 31) wide = true;
-                else atomicMax(&h.bw[key >> 32], (unsigned)t);
+                const K key = h.key[i];
+                if (key == T::kEmpty) continue;
+                const V t = h.val[i];
+                if (!NARROW && (t >> 31)) wide = true;
+                else atomicMax(&h.bw[T::row(key)], (unsigned)t);
             }
-            if (__any_sync(0xffffffffu, wide)) {
+            if (!NARROW && __any_sync(0xffffffffu, wide)) {
                 __syncwarp();
                 if (lane == 0) {
                     for (int i = 0; i < kLpHash; ++i) {
-                        const unsigned long long key = h.key[i];
-                        if (key == kLpEmpty) continue;
-                        const int r = (int)(key >> 32);
-                        const int l = (int)(unsigned)key;
+                        const K key = h.key[i];
+                        if (key == T::kEmpty) continue;
+                        const int r = T::row(key);
+                        const int l = T::lab(key);
                         if (lp_better((long long)h.val[i], l, h.wide_w[r], h.bl[r])) {
                             h.wide_w[r] = (long long)h.val[i];
                             h.bl[r] = l;
                         }
-                        h.key[i] = kLpEmpty;
+                        h.key[i] = T::kEmpty;
                         h.val[i] = 0;
                     }
                 }
@@ -187,11 +240,11 @@ k_lp_warp(const int *__restrict__ rp, const int2 *__restrict__ adj, int n, const
                 __syncwarp();
                 // pass 2: the smallest label reaching it; empty the table
                 for (int i = lane; i < kLpHash; i += 32) {
-                    const unsigned long long key = h.key[i];
-                    if (key != kLpEmpty) {
-                        const int r = (int)(key >> 32);
-                        if (h.val[i] == (unsigned long long)h.bw[r]) atomicMin(&h.bl[r], (int)(unsigned)key);
-                        h.key[i] = kLpEmpty;
+                    const K key = h.key[i];
+                    if (key != T::kEmpty) {
+                        const int r = T::row(key);
+                        if (h.val[i] == (V)h.bw[r]) atomicMin(&h.bl[r], T::lab(key));
+                        h.key[i] = T::kEmpty;
                         h.val[i] = 0;
                     }
                 }
@@ -256,12 +309,23 @@ k_lp_big(const int *__restrict__ rp, const int2 *__restrict__ adj, const int *__
     }
 }
 
-__global__ void k_max_row(const int *__restrict__ rp, int n, int *out) {
+// longest row (*out) and largest weighted degree (*out_deg)
+__global__ void k_max_row(const int *__restrict__ rp, const i64 *__restrict__ deg, int n, int *out,
+                          unsigned long long *out_deg) {
     int best = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    long long bd = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         best = max(best, rp[v + 1] - rp[v]);
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+        bd = max(bd, (long long)deg[v]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        bd = max(bd, __shfl_xor_sync(0xffffffffu, bd, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, best);
+        atomicMax(out_deg, (unsigned long long)bd);
+    }
 }
 
 }  // namespace
@@ -275,12 +339,16 @@ int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cud
     if (iters <= 0 || n == 0) return MC_OK;
     int *d_cnt = reinterpret_cast<int *>(&w.st->count);      // hubs this half-sweep
     int *d_max = reinterpret_cast<int *>(&w.st->count2);     // longest row
-    MC_CUDA(cudaMemsetAsync(&w.st->count2, 0, sizeof(long long), s));
+    MC_CUDA(cudaMemsetAsync(&w.st->count, 0, 2 * sizeof(long long), s));
     int blocks_v = (n + 255) / 256;
     if (blocks_v > num_sms() * 8) blocks_v = num_sms() * 8;
-    ++::mc::g_launches; k_max_row<<<blocks_v, 256, 0, s>>>(g.rp, n, d_max);
+    ++::mc::g_launches;
+    k_max_row<<<blocks_v, 256, 0, s>>>(g.rp, g.deg, n, d_max, reinterpret_cast<unsigned long long *>(&w.st->count));
     MC_TRY(status_read(w, s));
     const int maxrow = (int)w.h_st->count2;
+    // 32-bit hash entries: labels < 2^27, and a row's total per label is at
+    // most its weighted degree
+    const bool narrow = n < (1 << 27) && w.h_st->count < (1LL << 31);
     // hub hash slices: 2^k >= twice the longest row slots each (an empty
     // slot always ends a probe), as many slices as fit in one radix buffer
     // (u64 weights in the key buffer, int keys in the value buffer)
@@ -297,12 +365,19 @@ int label_prop(const DevGraph &g, Work &w, int iters, u64 seed, int *labels, cud
         return MC_ENOMEM;
     }
     int *cur = labels, *nxt = w.cnt;
-    int grid = num_sms() * 6;
+    // as many blocks as stay resident (the narrow kernel fits about twice as many)
+    int per_sm = 0;
+    if (narrow) MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp_warp<true>, kLpWarps * 32, 0));
+    else MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp_warp<false>, kLpWarps * 32, 0));
+    const int grid = num_sms() * (per_sm > 0 ? per_sm : 1);
     for (int it = 0; it < iters; ++it) {
         for (int half = 0; half < 2; ++half) {
             MC_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
             ++::mc::g_launches;
-            k_lp_warp<<<grid, kLpWarps * 32, 0, s>>>(g.rp, g.adj, n, cur, nxt, seed, it, half, w.T, d_cnt);
+            if (narrow)
+                k_lp_warp<true><<<grid, kLpWarps * 32, 0, s>>>(g.rp, g.adj, n, cur, nxt, seed, it, half, w.T, d_cnt);
+            else
+                k_lp_warp<false><<<grid, kLpWarps * 32, 0, s>>>(g.rp, g.adj, n, cur, nxt, seed, it, half, w.T, d_cnt);
             if (hubs) {
                 ++::mc::g_launches;
                 k_lp_big<<<(int)hub_blocks, kLpBigThreads, 0, s>>>(g.rp, g.adj, cur, nxt, w.T, d_cnt,
