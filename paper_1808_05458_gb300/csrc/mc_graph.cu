@@ -567,6 +567,41 @@ __global__ void k_check_sym(const DevGraph g, int *err, unsigned long long *up,
     }
 }
 
+// The same check on canonical input straight from its own arrays: the
+// searches read the 4-byte neighbour ids instead of the 8-byte {neighbour,
+// weight} arcs (fewer sectors per search), and weights only where a mirror
+// is found (w == nullptr: every weight is 1).
+__global__ void k_check_sym_raw(const int *__restrict__ src, const int *__restrict__ rp,
+                                const int *__restrict__ col, const int *__restrict__ w, i64 arcs, int *err,
+                                unsigned long long *up, unsigned long long *down) {
+    long long nu = 0, nd = 0;
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < arcs; j += (i64)gridDim.x * blockDim.x) {
+        const int u = src[j], v = col[j];
+        if (u < v) {
+            ++nu;
+            int lo = rp[v], hi = rp[v + 1] - 1, found = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int x = col[mid];
+                if (x == u) { found = mid; break; }
+                if (x < u) lo = mid + 1; else hi = mid - 1;
+            }
+            if (found < 0 || (w && w[found] != w[j])) atomicOr(err, kErrAsym);
+        } else {
+            ++nd;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nu) atomicAdd(up, (unsigned long long)nu);
+        if (nd) atomicAdd(down, (unsigned long long)nd);
+    }
+}
+
 __global__ void k_clear_err(Status *st) { st->err = 0; }
 
 // Raw CSR -> graph (sources, {neighbour, weight}, degrees) in one pass,
@@ -619,7 +654,8 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     if (wk.h_st->err) return MC_EINVAL;
     out.n = n;
     out.arcs = arcs_raw;
-    if (wk.h_st->count2 != 0) {
+    const bool canonical_input = wk.h_st->count2 == 0;
+    if (!canonical_input) {
         ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
         ++::mc::g_launches; k_emit_raw<<<grid_for(((i64)arcs_raw + kEmitItems - 1) / kEmitItems), kThreads, 0, s>>>(
             rp, col, w, n, arcs_raw, wk.keysA, wk.valsA, reinterpret_cast<u64 *>(&wk.st->count), &wk.st->err);
@@ -631,9 +667,14 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     }
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
     if (check_sym && out.arcs > 0) {
-        ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(
-            out, &wk.st->err, reinterpret_cast<unsigned long long *>(&wk.st->count),
-            reinterpret_cast<unsigned long long *>(&wk.st->count2));
+        auto *up = reinterpret_cast<unsigned long long *>(&wk.st->count);
+        auto *down = reinterpret_cast<unsigned long long *>(&wk.st->count2);
+        ++::mc::g_launches;
+        if (canonical_input)
+            k_check_sym_raw<<<grid_for(out.arcs), kThreads, 0, s>>>(out.src, rp, col, w, out.arcs, &wk.st->err, up,
+                                                                    down);
+        else
+            k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err, up, down);
         MC_CUDA(cudaGetLastError());
     }
     MC_TRY(status_read(wk, s));

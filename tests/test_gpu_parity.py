@@ -565,6 +565,32 @@ def test_invalid_inputs(mc):
         mc.Graph(badrp, col, w)
 
 
+def test_asymmetric_graph_rejected(mc):
+    # canonical input (sorted rows) is checked on its own arrays, other input
+    # on its canonical form; both refuse a missing mirror or a mirror of
+    # another weight, with and without a weight array
+    g = graphgen.random_connected(300, 900, seed=3, wmax=9)
+    rp, col, w = (np.asarray(a, dtype=np.int32) for a in oracle.contract(*g, np.arange(300, dtype=np.int32), 300))
+    assert all((np.diff(col[rp[v]:rp[v + 1]]) > 0).all() for v in range(300))  # canonical as given
+    with mc.Graph(rp, col, w) as G:
+        assert G.min_cut().lam == oracle.noi(rp, col, w)[0]
+    w_bad = w.copy()
+    w_bad[5] += 1
+    rp_d = np.array([0, 1, 2, 3], dtype=np.int32)    # 0 -> 1, 1 -> 0, and 2 -> 0 unmirrored
+    col_d = np.array([1, 0, 0], dtype=np.int32)
+    for args in ((rp, col, w_bad), (rp_d, col_d, np.ones(3, dtype=np.int32)), (rp_d, col_d, None)):
+        with pytest.raises(mc.MinCutError) as e:
+            mc.Graph(*args)
+        assert e.value.code == mc.MC_EINVAL
+    # the same weight mismatch with a reversed row (not canonical as given)
+    col_r, w_r = col.copy(), w_bad.copy()
+    col_r[rp[0]:rp[1]] = col_r[rp[0]:rp[1]][::-1].copy()
+    w_r[rp[0]:rp[1]] = w_r[rp[0]:rp[1]][::-1].copy()
+    with pytest.raises(mc.MinCutError) as e:
+        mc.Graph(rp, col_r, w_r)
+    assert e.value.code == mc.MC_EINVAL
+
+
 def _check_batch_sides(b, lam, bits, boff, ks):
     for k in ks:
         g = graphgen.batch_graph(b, k)
