@@ -175,16 +175,66 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
         return rc;
     }
     const int *drp = row_ptr, *dcol = col, *dw = w;
+    // host input: the raw arrays are staged in Ga (rp, src) and Gb (src);
+    // the arcs go in kStageChunks chunks of whole rows on a copy stream, so
+    // that each chunk is canonicalised while the next one is on the way
+    constexpr int kStageChunks = 4;
+    StagedInput staged;
+    int row_split[kStageChunks + 1];
+    cudaEvent_t ready[kStageChunks] = {};
+    cudaStream_t cs = nullptr;
+    struct StageFree {
+        cudaEvent_t *ev;
+        cudaStream_t *cs;
+        ~StageFree() {
+            for (int k = 0; k < kStageChunks; ++k)
+                if (ev[k]) cudaEventDestroy(ev[k]);
+            if (*cs) cudaStreamDestroy(*cs);
+        }
+    } stage_free{ready, &cs};
     if (!dev) {
-        // stage the raw arrays in Ga (rp, src) and Gb (src)
         cudaError_t e = cudaMemcpyAsync(g->Ga.rp, row_ptr, sizeof(int) * ((size_t)n + 1),
                                         cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && arcs_raw > 0)
-            e = cudaMemcpyAsync(g->Ga.src, col, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && arcs_raw > 0 && w)
-            e = cudaMemcpyAsync(g->Gb.src, w, sizeof(int) * (size_t)arcs_raw, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && arcs_raw > 0) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess && arcs_raw > 0) {
+            // row splits at about equal arc counts (a search over the host
+            // offsets; they are validated on the device before any chunk is
+            // read)
+            row_split[0] = 0;
+            for (int k = 1; k < kStageChunks; ++k) {
+                const i64 target = (i64)arcs_raw * k / kStageChunks;
+                int lo = row_split[k - 1], hi = n;
+                while (lo < hi) {
+                    const int mid = lo + (hi - lo + 1) / 2;
+                    if ((i64)row_ptr[mid] <= target) lo = mid; else hi = mid - 1;
+                }
+                row_split[k] = lo;
+            }
+            row_split[kStageChunks] = n;
+            for (int k = 0; k < kStageChunks && e == cudaSuccess; ++k) {
+                // clamped: offsets that fail the device check never reach a
+                // build, but their copies must stay inside both buffers
+                i64 a0 = k == 0 ? 0 : row_ptr[row_split[k]];
+                i64 a1 = k == kStageChunks - 1 ? arcs_raw : row_ptr[row_split[k + 1]];
+                a0 = a0 < 0 ? 0 : (a0 > arcs_raw ? arcs_raw : a0);
+                a1 = a1 < a0 ? a0 : (a1 > arcs_raw ? arcs_raw : a1);
+                e = cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming);
+                if (e == cudaSuccess && a1 > a0)
+                    e = cudaMemcpyAsync(g->Ga.src + a0, col + a0, sizeof(int) * (size_t)(a1 - a0),
+                                        cudaMemcpyHostToDevice, cs);
+                if (e == cudaSuccess && a1 > a0 && w)
+                    e = cudaMemcpyAsync(g->Gb.src + a0, w + a0, sizeof(int) * (size_t)(a1 - a0),
+                                        cudaMemcpyHostToDevice, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(ready[k], cs);
+            }
+            staged.chunks = kStageChunks;
+            staged.row_split = row_split;
+            staged.ready = ready;
+        }
+        staged.arcs = arcs_raw;
         if (e != cudaSuccess) {
             set_cuda_error(e, "cudaMemcpyAsync(input)");
+            if (cs) cudaStreamSynchronize(cs);
             destroy_all(g);
             return MC_ECUDA;
         }
@@ -192,7 +242,10 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
         dcol = g->Ga.src;
         dw = w ? g->Gb.src : nullptr;
     }
-    rc = canonicalize(n, drp, dcol, dw, (flags & MC_TRUST_INPUT) == 0, g->G0, g->w, s);
+    rc = canonicalize(n, drp, dcol, dw, (flags & MC_TRUST_INPUT) == 0, g->G0, g->w, s, dev ? nullptr : &staged);
+    // the copy stream has finished before the stage is freed (canonicalize
+    // waited on its last event, or the error path waits here)
+    if (cs) cudaStreamSynchronize(cs);
     if (rc == MC_OK) rc = min_degree(g->G0, g->w, s);
     if (rc == MC_OK) rc = graph_stats(g->G0, g->w, s);
     if (rc == MC_OK) rc = status_read(g->w, s);

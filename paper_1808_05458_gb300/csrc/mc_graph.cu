@@ -610,11 +610,12 @@ __global__ void k_clear_err(Status *st) { st->err = 0; }
 // graph) and whether it is invalid (range, negative weight).  One warp per
 // row.  w == nullptr: an unweighted graph, every arc of weight 1.
 __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict__ col,
-                              const int *__restrict__ w, int n, DevGraph out, int *err, int *noncanon) {
+                              const int *__restrict__ w, int n, int u_lo, int u_hi, DevGraph out, int *err,
+                              int *noncanon) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     bool bad = false;
-    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    for (int u = u_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < u_hi; u += nw) {
         const int a0 = rp[u], a1 = rp[u + 1];
         long long d = 0;
         for (int i = a0 + lane; i < a1; i += 32) {
@@ -634,21 +635,37 @@ __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict_
 }
 
 int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym, DevGraph &out,
-                 Work &wk, cudaStream_t s) {
+                 Work &wk, cudaStream_t s, const StagedInput *staged) {
     ++::mc::g_launches; k_clear_err<<<1, 1, 0, s>>>(wk.st);
     ++::mc::g_launches; k_check_rp<<<grid_for(n), kThreads, 0, s>>>(rp, n, &wk.st->err);
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err) return MC_EINVAL;
     int arcs_raw = 0;
-    MC_CUDA(cudaMemcpyAsync(&arcs_raw, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MC_CUDA(cudaStreamSynchronize(s));
+    if (staged) {
+        arcs_raw = (int)staged->arcs;
+    } else {
+        MC_CUDA(cudaMemcpyAsync(&arcs_raw, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+    }
     if (arcs_raw < 0 || (i64)arcs_raw > wk.cap_arcs) return MC_EINVAL;
-    // already canonical (the common case): built directly, no sort
+    // already canonical (the common case): built directly, no sort; staged
+    // input chunk by chunk as it lands
     int *noncanon = reinterpret_cast<int *>(&wk.st->count2);
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
     MC_CUDA(cudaMemcpyAsync(out.rp, rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
-    ++::mc::g_launches; k_build_canon<<<grid_for((i64)n * 32), kThreads, 0, s>>>(rp, col, w, n, out, &wk.st->err,
-                                                                               noncanon);
+    if (staged && staged->chunks > 0) {
+        for (int k = 0; k < staged->chunks; ++k) {
+            MC_CUDA(cudaStreamWaitEvent(s, staged->ready[k], 0));
+            const int lo = staged->row_split[k], hi = staged->row_split[k + 1];
+            if (hi <= lo) continue;
+            ++::mc::g_launches;
+            k_build_canon<<<grid_for((i64)(hi - lo) * 32), kThreads, 0, s>>>(rp, col, w, n, lo, hi, out,
+                                                                          &wk.st->err, noncanon);
+        }
+    } else {
+        ++::mc::g_launches;
+        k_build_canon<<<grid_for((i64)n * 32), kThreads, 0, s>>>(rp, col, w, n, 0, n, out, &wk.st->err, noncanon);
+    }
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(wk, s));
     if (wk.h_st->err) return MC_EINVAL;

@@ -182,8 +182,18 @@ int contract_graph(const DevGraph &in, DevGraph &out, Work &w, i64 clamp, bool f
 
 // canonicalise raw CSR arrays (device) into `out` (drops self-loops / zero
 // weights, sums parallel arcs, sorts rows); checks symmetry if asked.
+// Input still arriving from the host, in chunks of whole rows: chunk k holds
+// rows [row_split[k], row_split[k + 1]) and is on the device once ready[k]
+// has fired; arcs is the input's arc count (known on the host).
+struct StagedInput {
+    int chunks = 0;
+    const int *row_split = nullptr;
+    cudaEvent_t *ready = nullptr;
+    i64 arcs = 0;
+};
 int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym,
-                 DevGraph &out, Work &wk, cudaStream_t s);
+                 DevGraph &out, Work &wk, cudaStream_t s,
+                 const StagedInput *staged = nullptr);
 
 int union_find_init(int *par, int n, cudaStream_t s);
 int connected_components(const DevGraph &g, Work &w, int *ncomp, cudaStream_t s);
