@@ -567,54 +567,31 @@ __global__ void k_check_sym(const DevGraph g, int *err, unsigned long long *up,
     }
 }
 
-// The same check on canonical input straight from its own arrays: the
-// searches read the 4-byte neighbour ids instead of the 8-byte {neighbour,
-// weight} arcs (fewer sectors per search), and weights only where a mirror
-// is found (w == nullptr: every weight is 1).
-__global__ void k_check_sym_raw(const int *__restrict__ src, const int *__restrict__ rp,
-                                const int *__restrict__ col, const int *__restrict__ w, i64 arcs, int *err,
-                                unsigned long long *up, unsigned long long *down) {
-    long long nu = 0, nd = 0;
-    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < arcs; j += (i64)gridDim.x * blockDim.x) {
-        const int u = src[j], v = col[j];
-        if (u < v) {
-            ++nu;
-            int lo = rp[v], hi = rp[v + 1] - 1, found = -1;
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int x = col[mid];
-                if (x == u) { found = mid; break; }
-                if (x < u) lo = mid + 1; else hi = mid - 1;
-            }
-            if (found < 0 || (w && w[found] != w[j])) atomicOr(err, kErrAsym);
-        } else {
-            ++nd;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        nu += __shfl_xor_sync(0xffffffffu, nu, o);
-        nd += __shfl_xor_sync(0xffffffffu, nd, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (nu) atomicAdd(up, (unsigned long long)nu);
-        if (nd) atomicAdd(down, (unsigned long long)nd);
-    }
+__global__ void k_clear_err(Status *st) {
+    st->err = 0;
+    st->sym_up = 0;
+    st->sym_down = 0;
+    st->sym_bad = 0;
 }
-
-__global__ void k_clear_err(Status *st) { st->err = 0; }
 
 // Raw CSR -> graph (sources, {neighbour, weight}, degrees) in one pass,
 // flagging whether the input was canonical already (rows strictly
 // increasing, no self-loop, weights > 0; if not, the sort path rebuilds the
 // graph) and whether it is invalid (range, negative weight).  One warp per
 // row.  w == nullptr: an unweighted graph, every arc of weight 1.
+// With `check`, the symmetry of input that turns out canonical is checked on
+// the way (rows < u are complete whenever row u is, also when the input
+// arrives in chunks of rows): every downward arc (u, v, c), v < u, must find
+// its mirror (v, u, c) in v's row, and as many arcs must run up as down (the
+// mirror map is then a bijection).  Neighbour ids are 4 bytes here, so a
+// search reads fewer sectors than in the built 8-byte arcs.
 __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict__ col,
                               const int *__restrict__ w, int n, int u_lo, int u_hi, DevGraph out, int *err,
-                              int *noncanon) {
+                              int *noncanon, Status *sym) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    bool bad = false;
+    bool bad = false, asym = false;
+    long long nu = 0, nd = 0;
     for (int u = u_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < u_hi; u += nw) {
         const int a0 = rp[u], a1 = rp[u + 1];
         long long d = 0;
@@ -626,12 +603,40 @@ __global__ void k_build_canon(const int *__restrict__ rp, const int *__restrict_
             out.src[i] = u;
             out.adj[i] = make_int2(v, c);
             d += c;
+            if (sym && v >= 0 && v < n) {
+                if (v > u) {
+                    ++nu;
+                } else if (v < u) {
+                    ++nd;
+                    int lo = rp[v], hi = rp[v + 1] - 1, found = -1;
+                    while (lo <= hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const int x = col[mid];
+                        if (x == u) { found = mid; break; }
+                        if (x < u) lo = mid + 1; else hi = mid - 1;
+                    }
+                    asym |= found < 0 || (w ? w[found] : 1) != c;
+                }
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0) out.deg[u] = d;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(noncanon, 1);
+    if (sym) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nu += __shfl_xor_sync(0xffffffffu, nu, o);
+            nd += __shfl_xor_sync(0xffffffffu, nd, o);
+        }
+        const bool any_asym = __any_sync(0xffffffffu, asym);
+        if (lane == 0) {
+            if (nu) atomicAdd(reinterpret_cast<unsigned long long *>(&sym->sym_up), (unsigned long long)nu);
+            if (nd) atomicAdd(reinterpret_cast<unsigned long long *>(&sym->sym_down), (unsigned long long)nd);
+            if (any_asym) atomicOr(&sym->sym_bad, 1);
+        }
+    }
 }
 
 int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_sym, DevGraph &out,
@@ -651,6 +656,7 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
     // already canonical (the common case): built directly, no sort; staged
     // input chunk by chunk as it lands
     int *noncanon = reinterpret_cast<int *>(&wk.st->count2);
+    Status *sym = check_sym ? wk.st : nullptr;  // zeroed with the error bits
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
     MC_CUDA(cudaMemcpyAsync(out.rp, rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
     if (staged && staged->chunks > 0) {
@@ -660,11 +666,12 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
             if (hi <= lo) continue;
             ++::mc::g_launches;
             k_build_canon<<<grid_for((i64)(hi - lo) * 32), kThreads, 0, s>>>(rp, col, w, n, lo, hi, out,
-                                                                          &wk.st->err, noncanon);
+                                                                          &wk.st->err, noncanon, sym);
         }
     } else {
         ++::mc::g_launches;
-        k_build_canon<<<grid_for((i64)n * 32), kThreads, 0, s>>>(rp, col, w, n, 0, n, out, &wk.st->err, noncanon);
+        k_build_canon<<<grid_for((i64)n * 32), kThreads, 0, s>>>(rp, col, w, n, 0, n, out, &wk.st->err, noncanon,
+                                                                  sym);
     }
     MC_CUDA(cudaGetLastError());
     MC_TRY(status_read(wk, s));
@@ -682,16 +689,16 @@ int canonicalize(int n, const int *rp, const int *col, const int *w, bool check_
         const i64 m = wk.h_st->count;
         MC_TRY(build_from_pairs(m, n, LLONG_MAX, out, wk, s, {}));
     }
+    if (canonical_input) {
+        // checked while it was built
+        if (check_sym && (wk.h_st->sym_bad || wk.h_st->sym_up != wk.h_st->sym_down)) return MC_EINVAL;
+        return MC_OK;
+    }
     ++::mc::g_launches; k_zero_count<<<1, 1, 0, s>>>(wk.st);
     if (check_sym && out.arcs > 0) {
         auto *up = reinterpret_cast<unsigned long long *>(&wk.st->count);
         auto *down = reinterpret_cast<unsigned long long *>(&wk.st->count2);
-        ++::mc::g_launches;
-        if (canonical_input)
-            k_check_sym_raw<<<grid_for(out.arcs), kThreads, 0, s>>>(out.src, rp, col, w, out.arcs, &wk.st->err, up,
-                                                                    down);
-        else
-            k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err, up, down);
+        ++::mc::g_launches; k_check_sym<<<grid_for(out.arcs), kThreads, 0, s>>>(out, &wk.st->err, up, down);
         MC_CUDA(cudaGetLastError());
     }
     MC_TRY(status_read(wk, s));

@@ -90,6 +90,10 @@ struct Status {
     int best_scan;      // scan whose alpha set lambda-hat (or -1)
     int best_len;       // prefix length of that scan
     int flip;           // the side bitmap's vertex-0 bit, before canonical polarity
+    // graph creation: arcs running up and down, and a missing or unequal
+    // mirror, seen while the input is built (valid when it is canonical)
+    i64 sym_up, sym_down;
+    int sym_bad, pad_;
 };
 
 constexpr int kErrAsym = 1;       // asymmetric input
