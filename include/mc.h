@@ -159,6 +159,13 @@ int mc_options_default(mc_options *opt);
 int mc_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col,
                     const int32_t *w, int32_t flags, mc_graph **out);
 
+/*
+ * mc_graph_destroy -- end a graph.  The device buffers and the stream of the
+ * last graph destroyed on a device (one per device, the largest so far) are
+ * kept for the next mc_graph_create on that device with at most its vertex
+ * and arc counts, which then allocates nothing; they stay held until a larger
+ * graph replaces them or the process exits.  Errors: MC_EINVAL for NULL.
+ */
 int mc_graph_destroy(mc_graph *g);
 
 /* Vertices and undirected edges of the canonical graph. */

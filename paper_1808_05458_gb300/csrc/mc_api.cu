@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "mc_internal.cuh"
@@ -29,6 +30,7 @@ struct mc_graph {
     i64 wmax0 = 0;          // largest arc weight of G0
     i64 two_arc_rows0 = 0;  // rows of G0 with exactly two arcs
     bool device_ptrs = false;
+    bool complete = false;  // every buffer allocated and the input built
     std::vector<cudaEvent_t> events;  // phase-clock events, reused across calls
 };
 
@@ -115,16 +117,6 @@ struct PhaseClock {
     }
 };
 
-int read_i32(const int *p, bool dev, int *out, cudaStream_t s) {
-    if (!dev) {
-        *out = *p;
-        return MC_OK;
-    }
-    MC_CUDA(cudaMemcpyAsync(out, p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MC_CUDA(cudaStreamSynchronize(s));
-    return MC_OK;
-}
-
 void destroy_all(mc_graph *g) {
     if (!g) return;
     cudaStream_t s = g->stream;
@@ -138,6 +130,42 @@ void destroy_all(mc_graph *g) {
     delete g;
 }
 
+// One destroyed graph per device is kept -- its stream, events and device
+// buffers -- for the next graph created on that device with at most its
+// vertex and arc counts (every buffer is sized by those two); a larger graph
+// replaces it.  Not while the allocation fault-injection hook is armed.
+struct ShellCache {
+    std::mutex m;
+    mc_graph *g[64] = {};
+};
+ShellCache g_shells;
+
+mc_graph *take_shell(int dev, int n, i64 arcs) {
+    if (dev < 0 || dev >= 64 || test_alloc_hook_armed()) return nullptr;
+    std::lock_guard<std::mutex> lock(g_shells.m);
+    mc_graph *c = g_shells.g[dev];
+    if (!c || c->w.cap_n < n || c->w.cap_arcs < arcs) return nullptr;
+    g_shells.g[dev] = nullptr;
+    return c;
+}
+
+// true if g was kept (its work on the stream finished first)
+bool park_shell(mc_graph *g) {
+    if (!g->complete || g->device < 0 || g->device >= 64 || test_alloc_hook_armed()) return false;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    mc_graph *old = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_shells.m);
+        mc_graph *&slot = g_shells.g[g->device];
+        if (slot && slot->w.cap_n >= g->w.cap_n && slot->w.cap_arcs >= g->w.cap_arcs) return false;
+        old = slot;
+        slot = g;
+    }
+    if (old) destroy_all(old);
+    return true;
+}
+
 cudaStream_t pick_stream(mc_graph *g, const mc_options *o) {
     return (o && o->cuda_stream) ? static_cast<cudaStream_t>(o->cuda_stream) : g->stream;
 }
@@ -147,33 +175,37 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
     if (!out || !row_ptr || n < 2) return MC_EINVAL;
     *out = nullptr;
     const bool dev = (flags & MC_DEVICE_PTRS) != 0;
-    mc_graph *g = new mc_graph();
-    g->device_ptrs = dev;
-    cudaGetDevice(&g->device);
-    {
+    int device = 0;
+    MC_CUDA(cudaGetDevice(&device));
+    int arcs_raw = 0;
+    if (dev) MC_CUDA(cudaMemcpy(&arcs_raw, row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+    else arcs_raw = row_ptr[n];
+    if (arcs_raw < 0 || (arcs_raw > 0 && !col)) return MC_EINVAL;
+    const i64 A = arcs_raw > 0 ? arcs_raw : 1;
+    int rc = MC_OK;
+    mc_graph *g = take_shell(device, n, A);
+    if (g) {
+        // a kept graph: its buffers are large enough; the input is built
+        // into them below
+        g->complete = false;
+    } else {
+        g = new mc_graph();
+        g->device = device;
         cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             set_cuda_error(e, "cudaStreamCreate");
             delete g;
             return MC_ECUDA;
         }
+        if ((rc = work_alloc(g->w, n, A, g->stream)) != MC_OK || (rc = graph_alloc(g->G0, n, A, g->stream)) != MC_OK ||
+            (rc = graph_alloc(g->Ga, n, A, g->stream)) != MC_OK || (rc = graph_alloc(g->Gb, n, A, g->stream)) != MC_OK) {
+            destroy_all(g);
+            return rc;
+        }
     }
-    cudaStream_t s = g->stream;
-    int arcs_raw = 0;
-    int rc = read_i32(row_ptr + n, dev, &arcs_raw, s);
-    if (rc == MC_OK && arcs_raw < 0) rc = MC_EINVAL;
-    if (rc == MC_OK && arcs_raw > 0 && !col) rc = MC_EINVAL;
-    if (rc != MC_OK) {
-        destroy_all(g);
-        return rc;
-    }
-    const i64 A = arcs_raw > 0 ? arcs_raw : 1;
+    g->device_ptrs = dev;
     g->n0 = n;
-    if ((rc = work_alloc(g->w, n, A, s)) != MC_OK || (rc = graph_alloc(g->G0, n, A, s)) != MC_OK ||
-        (rc = graph_alloc(g->Ga, n, A, s)) != MC_OK || (rc = graph_alloc(g->Gb, n, A, s)) != MC_OK) {
-        destroy_all(g);
-        return rc;
-    }
+    cudaStream_t s = g->stream;
     const int *drp = row_ptr, *dcol = col, *dw = w;
     // host input: the raw arrays are staged in Ga (rp, src) and Gb (src);
     // the arcs go in kStageChunks chunks of whole rows on a copy stream, so
@@ -261,6 +293,7 @@ int create_impl(int32_t n, const int32_t *row_ptr, const int32_t *col, const int
         return rc;
     }
     g->arcs0 = g->G0.arcs;
+    g->complete = true;
     *out = g;
     return MC_OK;
 }
@@ -648,7 +681,7 @@ int mc_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col, const
 
 int mc_graph_destroy(mc_graph *g) {
     if (!g) return MC_EINVAL;
-    destroy_all(g);
+    if (!park_shell(g)) destroy_all(g);
     return MC_OK;
 }
 

@@ -55,6 +55,7 @@ void set_error_detail(const char *msg);
 // the graph's stream; buffers live as long as their owning mc_graph.
 int dev_alloc(void **p, size_t bytes, cudaStream_t s);
 void test_fail_alloc_after(long long k);  // mc_test_fail_alloc_after
+bool test_alloc_hook_armed();               // the hook counts allocations now
 void dev_free(void *p, cudaStream_t s);
 
 template <class T>

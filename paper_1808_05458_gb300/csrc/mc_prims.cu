@@ -44,6 +44,7 @@ static void retain_pool_memory() {
 static std::atomic<long long> g_fail_alloc_after{-1};
 
 void test_fail_alloc_after(long long k) { g_fail_alloc_after.store(k < 0 ? -1 : k); }
+bool test_alloc_hook_armed() { return g_fail_alloc_after.load() >= 0; }
 
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     long long k = g_fail_alloc_after.load();
