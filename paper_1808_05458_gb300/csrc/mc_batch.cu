@@ -619,10 +619,77 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     const int *col_in = B.col + a0, *w_in = B.w + a0;
     int err = 0;
     int ovf = 0;
+    long long arcs = 0;
+
+    // Input that is canonical as given (rows strictly increasing, no
+    // self-loop, positive weights, neighbours in range) is copied into A in
+    // one arc-parallel pass: each arc's row by binary search in the offsets,
+    // the degrees by a segmented sum over the lanes of a row.  The same pass
+    // checks symmetry: every downward arc (v < u) finds its mirror with the
+    // same weight by binary search in row v, and the upward and downward
+    // arcs are equally many (rows hold no duplicates, so the mirror map is
+    // then a bijection).  Other input takes the general path below (drop,
+    // sort, merge, symmetry check).
+    const int m_raw = __ldg(rp_in + n0);
+    for (int v = lane; v < n0; v += 32) S.deg[v] = 0;
+    __syncwarp();
+    bool canon = m_raw >= 0;
+    bool sym_ok = true;
+    int ups = 0, downs = 0;
+    for (int i0 = 0; i0 < m_raw && canon; i0 += 32) {
+        const int i = i0 + lane;
+        int u = -1, v = -1, c = 0;
+        bool ok = true;
+        if (i < m_raw) {
+            int lo = 0, hi = n0 - 1;  // largest u with rp_in[u] <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(rp_in + mid) <= i) lo = mid; else hi = mid - 1;
+            }
+            u = lo;
+            v = col_in[i];
+            c = w_in[i];
+        }
+        const int pu = __shfl_up_sync(0xffffffffu, u, 1), pv = __shfl_up_sync(0xffffffffu, v, 1);
+        if (i < m_raw) {
+            int prev = -1;  // the row's previous neighbour
+            if (i > __ldg(rp_in + u)) prev = lane > 0 && pu == u ? pv : col_in[i - 1];
+            ok = v >= 0 && v < n0 && v != u && c > 0 && prev < v;
+            S.srcA[i] = u;
+            S.adjA[i] = make_int2(v, c);
+            if (ok && v < u) {
+                ++downs;
+                int lo = __ldg(rp_in + v), hi = __ldg(rp_in + v + 1) - 1;  // find u in row v
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (col_in[mid] < u) lo = mid + 1; else hi = mid;
+                }
+                if (lo > hi || col_in[lo] != u || w_in[lo] != c) sym_ok = false;
+            } else if (ok) {
+                ++ups;
+            }
+        }
+        // the lanes of one row add their weights toward its first lane
+        long long cs = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_down_sync(0xffffffffu, cs, o);
+            const int tu = __shfl_down_sync(0xffffffffu, u, o);
+            if (lane + o < 32 && tu == u) cs += t;
+        }
+        if (u >= 0 && (lane == 0 || pu != u)) atomicAdd(reinterpret_cast<unsigned long long *>(&S.deg[u]), (unsigned long long)cs);
+        canon = __all_sync(0xffffffffu, ok);
+    }
+    if (canon) {
+        for (int v = lane; v <= n0; v += 32) S.rpA[v] = __ldg(rp_in + v);
+        arcs = m_raw;
+        if (!__all_sync(0xffffffffu, sym_ok) || warp_sum_ll(ups) != warp_sum_ll(downs)) err = MC_EINVAL;
+        __syncwarp();
+    }
 
     // raw arcs -> (srcB, adjB), dropping self-loops and zero weights
     long long m = 0;
-    for (int u = 0; u < n0; ++u) {
+    for (int u = 0; u < n0 && !canon; ++u) {
         const int lo = rp_in[u], hi = rp_in[u + 1];
         for (int e0 = lo; e0 < hi; e0 += 32) {
             const int e = e0 + lane;
@@ -645,15 +712,17 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
         }
     }
     err = __reduce_or_sync(0xffffffffu, err);
-    // canonical CSR in A (identity labels)
-    for (int v = lane; v < n0; v += 32) S.lab[v] = v;
-    __syncwarp();
-    long long arcs = warp_contract(S.srcB, S.adjB, m, S.lab, n0, kInt32Max, S.rpT, S.adjT, S.rpA,
-                                   S.srcA, S.adjA, S.deg, S.cnt, S.mark, &ovf);
-    if (__reduce_or_sync(0xffffffffu, ovf)) err = MC_EOVERFLOW;
+    if (!canon) {
+        // canonical CSR in A (identity labels)
+        for (int v = lane; v < n0; v += 32) S.lab[v] = v;
+        __syncwarp();
+        arcs = warp_contract(S.srcB, S.adjB, m, S.lab, n0, kInt32Max, S.rpT, S.adjT, S.rpA, S.srcA, S.adjA, S.deg,
+                             S.cnt, S.mark, &ovf);
+        if (__reduce_or_sync(0xffffffffu, ovf)) err = MC_EOVERFLOW;
+    }
     // an arc without its mirror (same weight after merging) is malformed
     // input: the raw-arc buffers (B) and the sort buffers (T) are free here
-    if (!err &&
+    if (!err && !canon &&
         !warp_symmetric(S.rpA, S.srcA, S.adjA, arcs, n0, S.rpT, S.srcB, S.adjB, S.rpB, S.eslot, S.adjT, S.cnt,
                         S.mark))
         err = MC_EINVAL;
