@@ -623,65 +623,110 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
 
     // Input that is canonical as given (rows strictly increasing, no
     // self-loop, positive weights, neighbours in range) is copied into A in
-    // one arc-parallel pass: each arc's row by binary search in the offsets,
-    // the degrees by a segmented sum over the lanes of a row.  The same pass
-    // checks symmetry: every downward arc (v < u) finds its mirror with the
-    // same weight by binary search in row v, and the upward and downward
-    // arcs are equally many (rows hold no duplicates, so the mirror map is
-    // then a bijection).  Other input takes the general path below (drop,
-    // sort, merge, symmetry check).
+    // one arc-parallel pass: each arc's row by binary search in the offsets
+    // (staged on chip when they fit), the degrees by a segmented sum over
+    // the lanes of a row.  The same pass checks symmetry: every downward arc
+    // (v < u) finds its mirror with the same weight by binary search in row
+    // v, and the upward and downward arcs are equally many (rows hold no
+    // duplicates, so the mirror map is then a bijection).  Each lane carries
+    // kCU arcs at once so that the searches' dependent loads overlap.  Other
+    // input takes the general path below (drop, sort, merge, symmetry check).
+    constexpr int kCU = 4;
     const int m_raw = __ldg(rp_in + n0);
+    const bool rp_on_chip = n0 < SN;
+    for (int v = lane; v <= n0; v += 32) {
+        const int r = __ldg(rp_in + v);
+        S.rpA[v] = r;
+        if (rp_on_chip) sm.r[v] = r;
+    }
     for (int v = lane; v < n0; v += 32) S.deg[v] = 0;
     __syncwarp();
+    const int *rps = rp_on_chip ? sm.r : rp_in;
+    int top_row = 1;  // the largest power of two <= n0 - 1 (n0 >= 2)
+    while (top_row * 2 <= n0 - 1) top_row *= 2;
     bool canon = m_raw >= 0;
     bool sym_ok = true;
     int ups = 0, downs = 0;
-    for (int i0 = 0; i0 < m_raw && canon; i0 += 32) {
-        const int i = i0 + lane;
-        int u = -1, v = -1, c = 0;
-        bool ok = true;
-        if (i < m_raw) {
-            int lo = 0, hi = n0 - 1;  // largest u with rp_in[u] <= i
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(rp_in + mid) <= i) lo = mid; else hi = mid - 1;
-            }
-            u = lo;
-            v = col_in[i];
-            c = w_in[i];
-        }
-        const int pu = __shfl_up_sync(0xffffffffu, u, 1), pv = __shfl_up_sync(0xffffffffu, v, 1);
-        if (i < m_raw) {
-            int prev = -1;  // the row's previous neighbour
-            if (i > __ldg(rp_in + u)) prev = lane > 0 && pu == u ? pv : col_in[i - 1];
-            ok = v >= 0 && v < n0 && v != u && c > 0 && prev < v;
-            S.srcA[i] = u;
-            S.adjA[i] = make_int2(v, c);
-            if (ok && v < u) {
-                ++downs;
-                int lo = __ldg(rp_in + v), hi = __ldg(rp_in + v + 1) - 1;  // find u in row v
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (col_in[mid] < u) lo = mid + 1; else hi = mid;
-                }
-                if (lo > hi || col_in[lo] != u || w_in[lo] != c) sym_ok = false;
-            } else if (ok) {
-                ++ups;
-            }
-        }
-        // the lanes of one row add their weights toward its first lane
-        long long cs = c;
+    for (int i0 = 0; i0 < m_raw && canon; i0 += 32 * kCU) {
+        int u[kCU], v[kCU], c[kCU];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_down_sync(0xffffffffu, cs, o);
-            const int tu = __shfl_down_sync(0xffffffffu, u, o);
-            if (lane + o < 32 && tu == u) cs += t;
+        for (int j = 0; j < kCU; ++j) {
+            const int i = i0 + 32 * j + lane;
+            u[j] = i < m_raw ? 0 : -1;
+            v[j] = i < m_raw ? col_in[i] : -1;
+            c[j] = i < m_raw ? w_in[i] : 0;
         }
-        if (u >= 0 && (lane == 0 || pu != u)) atomicAdd(reinterpret_cast<unsigned long long *>(&S.deg[u]), (unsigned long long)cs);
+        const int prev0 = lane == 0 && i0 > 0 ? col_in[i0 - 1] : -1;
+        // row of each arc: the largest u with rps[u] <= i
+        for (int step = top_row; step > 0; step >>= 1) {
+#pragma unroll
+            for (int j = 0; j < kCU; ++j) {
+                const int i = i0 + 32 * j + lane;
+                if (u[j] >= 0 && u[j] + step <= n0 - 1 && rps[u[j] + step] <= i) u[j] += step;
+            }
+        }
+        bool ok = true;
+        int base[kCU], len[kCU], cnt[kCU];
+        bool down[kCU];
+        unsigned maxlen = 0;
+#pragma unroll
+        for (int j = 0; j < kCU; ++j) {
+            const int i = i0 + 32 * j + lane;
+            int pv = __shfl_up_sync(0xffffffffu, v[j], 1);  // the previous arc's neighbour
+            const int last = __shfl_sync(0xffffffffu, v[(j + kCU - 1) % kCU], 31);
+            if (lane == 0) pv = j > 0 ? last : prev0;
+            down[j] = false;
+            len[j] = 0;
+            base[j] = 0;
+            cnt[j] = 0;
+            if (u[j] >= 0) {
+                const bool row_first = i == rps[u[j]];
+                const bool okj = v[j] >= 0 && v[j] < n0 && v[j] != u[j] && c[j] > 0 && (row_first || pv < v[j]);
+                ok = ok && okj;
+                S.srcA[i] = u[j];
+                S.adjA[i] = make_int2(v[j], c[j]);
+                if (okj && v[j] < u[j]) {
+                    ++downs;
+                    down[j] = true;
+                    base[j] = rps[v[j]];
+                    len[j] = rps[v[j] + 1] - base[j];
+                    maxlen = max(maxlen, (unsigned)len[j]);
+                } else if (okj) {
+                    ++ups;
+                }
+            }
+        }
+        // mirror of each downward arc: the entries of row v below u, counted
+        // by a branch-free binary search whose steps all lanes share
+        maxlen = __reduce_max_sync(0xffffffffu, maxlen);
+        int top_len = maxlen ? 1 : 0;
+        while (top_len && top_len * 2 <= (int)maxlen) top_len *= 2;
+        for (int step = top_len; step > 0; step >>= 1) {
+#pragma unroll
+            for (int j = 0; j < kCU; ++j)
+                if (cnt[j] + step <= len[j] && col_in[base[j] + cnt[j] + step - 1] < u[j]) cnt[j] += step;
+        }
+#pragma unroll
+        for (int j = 0; j < kCU; ++j) {
+            if (down[j]) {
+                const int at = base[j] + cnt[j];
+                if (cnt[j] >= len[j] || col_in[at] != u[j] || w_in[at] != c[j]) sym_ok = false;
+            }
+            // the lanes of one row add their weights toward its first lane
+            long long cs = c[j];
+            const int pu = __shfl_up_sync(0xffffffffu, u[j], 1);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_down_sync(0xffffffffu, cs, o);
+                const int tu = __shfl_down_sync(0xffffffffu, u[j], o);
+                if (lane + o < 32 && tu == u[j]) cs += t;
+            }
+            if (u[j] >= 0 && (lane == 0 || pu != u[j]))
+                atomicAdd(reinterpret_cast<unsigned long long *>(&S.deg[u[j]]), (unsigned long long)cs);
+        }
         canon = __all_sync(0xffffffffu, ok);
     }
     if (canon) {
-        for (int v = lane; v <= n0; v += 32) S.rpA[v] = __ldg(rp_in + v);
         arcs = m_raw;
         if (!__all_sync(0xffffffffu, sym_ok) || warp_sum_ll(ups) != warp_sum_ll(downs)) err = MC_EINVAL;
         __syncwarp();

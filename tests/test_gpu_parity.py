@@ -696,7 +696,9 @@ def test_batch_asymmetric_rejected(mc):
     # (as many arcs down as up fails)
     g_down = (np.array([0, 1, 2, 3], dtype=np.int32), np.array([1, 0, 0], dtype=np.int32),
               np.array([1, 1, 1], dtype=np.int32))
-    for bad in ((rp, col, w_bad), (rp_m, col_m, w_m), g_down):
+    # a downward arc whose mirror row is empty
+    g_empty = (np.array([0, 0, 1], dtype=np.int32), np.array([0], dtype=np.int32), np.array([4], dtype=np.int32))
+    for bad in ((rp, col, w_bad), (rp_m, col_m, w_m), g_down, g_empty):
         for graphs in ([bad], [good, bad, good]):
             with pytest.raises(mc.MinCutError) as ei:
                 mc.batch_min_cut(*_concat(graphs))
