@@ -33,8 +33,13 @@ constexpr int kBNB = 256;  // queue buckets per warp
 template <int SN>
 struct WarpSmem {
     int r[SN];
-    unsigned short eslot[SN + SN / 2];
-    unsigned short enext[SN + SN / 2];
+    union {
+        struct {
+            unsigned short eslot[SN + SN / 2];
+            unsigned short enext[SN + SN / 2];
+        } q;             // the bucket queue's entry pool
+        int rp[SN + 1];  // or the row offsets, for the dense on-chip scan
+    } u;
     int head[kBNB];
     int tail[kBNB];
     u32 bits[kBNB / 32];
@@ -488,6 +493,113 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
     }
 }
 
+// One full capped CAPFOREST scan (Alg. 3) of a graph held on chip (n <= SN
+// vertices, cap C < 2^25) with no queue beyond the r array itself: the
+// vertices fall into 32 groups of B consecutive ones (B a power of two,
+// B <= 64), and gmax[g] holds group g's largest key packed with its index,
+// (min(r, C) + 1) << 5 | (31 - g), 0 for a group with no reached vertex.  A
+// pop is two warp reductions: the best group, then the best vertex in it
+// (the smallest vertex of the largest key, as the other queues pop); the
+// same loads give the group's maximum without the popped vertex, and every
+// key rise is one shared atomicMax on its group's entry.  The row offsets
+// are staged on chip in the bucket queue's pool, which this scan leaves
+// unused, so a pop's only global round trip is its row's arcs.
+template <int SN>
+__device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, Counters &cnt) {
+    static_assert(SN <= 2048, "32 groups of at most 64 vertices");
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = lane_id();
+    int lgB = 0;
+    while ((32 << lgB) < n) ++lgB;
+    const int B = 1 << lgB;
+    int *r = sm.r;
+    int *rps = sm.u.rp;
+    u32 *gmax = reinterpret_cast<u32 *>(sm.head);
+    for (int v = lane; v <= n; v += 32) rps[v] = A.g.rp[v];
+    gmax[lane] = 0u;
+    __syncwarp();
+    long long L = ld_volatile_i64(&A.st->lam);
+    int Lj = L <= C ? (int)L : INT_MAX;  // the join threshold: none above C
+    long long alpha = 0, best = LLONG_MAX;
+    int nS = 0, best_len = 0;
+    bool alpha_ok = true;
+    cnt.scans++;
+    int p = start;
+    while (p >= 0 && nS < n) {
+        const int a0 = rps[p], a1 = rps[p + 1];
+        const int rx = r[p];
+        const long long dx = A.g.deg[p];
+        __syncwarp();
+        if (lane == 0) {
+            r[p] = kDone;
+            A.T[p] = 1;
+            A.order[p] = nS;
+        }
+        ++nS;
+        if (rx >= kSat) alpha_ok = false;
+        alpha += dx - 2LL * rx;
+        if (alpha_ok && nS < n && alpha < L) {
+            if (lane == 0) atomicMin(&A.st->lam, alpha);
+            best = alpha;
+            best_len = nS;
+            L = alpha;
+            Lj = L <= C ? (int)L : INT_MAX;
+        }
+        cnt.verts++;
+        cnt.arcs += a1 - a0;
+        __syncwarp();
+        int xh = p;
+        for (int i0 = a0; i0 < a1; i0 += 32) {
+            const int i = i0 + lane;
+            const int2 e = i < a1 ? A.g.adj[i] : make_int2(0, 0);
+            const int y = e.x;
+            bool join = false;
+            if (i < a1) {
+                const int ro = r[y];
+                if (ro != kDone) {
+                    const int rn = sat_add(ro, e.y);
+                    r[y] = rn;
+                    // a certificate min(r, C) only vouches for bounds <= C
+                    join = ro < Lj && Lj <= rn;
+                    const int ko = ro == 0 ? 0 : (ro < C ? ro : C) + 1, kn = (rn < C ? rn : C) + 1;
+                    if (ko != kn) atomicMax(&gmax[y >> lgB], ((u32)kn << 5) | (u32)(31 - (y >> lgB)));
+                }
+            }
+            int rt = INT_MAX;
+            if (join && uf_union_root(A.par, xh, y, &rt)) cnt.unions++;
+            rt = __reduce_min_sync(kAll, rt);
+            if (rt != INT_MAX) xh = rt;
+        }
+        __syncwarp();
+        // the next pop: best group, then its best vertex
+        const u32 top = __reduce_max_sync(kAll, gmax[lane]);
+        if (top == 0u) break;
+        const int g = 31 - (int)(top & 31u);
+        const int v0 = (g << lgB) + lane, v1 = v0 + 32;
+        u32 k0 = 0u, k1 = 0u;
+        if (lane < B && v0 < n) {
+            const int rv = r[v0];
+            if (rv != kDone && rv > 0) k0 = ((u32)((rv < C ? rv : C) + 1) << 6) | (u32)(63 - lane);
+        }
+        if (lane + 32 < B && v1 < n) {
+            const int rv = r[v1];
+            if (rv != kDone && rv > 0) k1 = ((u32)((rv < C ? rv : C) + 1) << 6) | (u32)(31 - lane);
+        }
+        const u32 m = __reduce_max_sync(kAll, k0 > k1 ? k0 : k1);
+        if (m == 0u) break;  // a group entry always has a reached member
+        p = (g << lgB) + 63 - (int)(m & 63u);
+        const u32 x0 = k0 == m ? 0u : k0, x1 = k1 == m ? 0u : k1;
+        const u32 m2 = __reduce_max_sync(kAll, x0 > x1 ? x0 : x1);
+        __syncwarp();
+        if (lane == 0) gmax[g] = m2 ? ((m2 >> 6) << 5) | (u32)(31 - g) : 0u;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        A.rec_alpha[1] = best;
+        A.rec_len[1] = best_len;
+    }
+}
+
 // one full capped CAPFOREST scan of the current graph (Alg. 3)
 template <int SN>
 __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, int n, long long arcs,
@@ -507,9 +619,11 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
     const int C = (int)(lam < (long long)0x7FFFFFFD ? lam : (long long)0x7FFFFFFD);
     if (in_smem && n <= 256 && C <= 63 && !fifo) {
         warp_scan_bits<SN>(A, sm, n, C, start, cnt);
+    } else if (in_smem && !fifo && C < (1 << 25)) {
+        warp_scan_dense<SN>(A, sm, n, C, start, cnt);
     } else if (in_smem) {
         BucketQ<unsigned short, kBNB> q;
-        q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.eslot; q.enext = sm.enext;
+        q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.u.q.eslot; q.enext = sm.u.q.enext;
         q.top = &sm.top; q.cap = SN + SN / 2; q.C = C; q.coarse = C + 1 > kBNB; q.fifo = fifo != 0;
         DenseTable tab{r, n};
         scan_one<DenseTable, BucketQ<unsigned short, kBNB>, false, true>(A, tab, q, start, 1, cnt);
