@@ -503,9 +503,13 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
 // same loads give the group's maximum without the popped vertex, and every
 // key rise is one shared atomicMax on its group's entry.  The row offsets
 // are staged on chip in the bucket queue's pool, which this scan leaves
-// unused, so a pop's only global round trip is its row's arcs.
+// unused, so a pop's only global round trip is its row's arcs.  A join
+// (r crossing the bound) only records its popped vertex in joinx[y] (a
+// vertex joins at most once a scan, as r only rises); the unions follow the
+// scan in one lane-parallel pass, off the pops' chain of latencies.
 template <int SN>
-__device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, Counters &cnt) {
+__device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, int *joinx,
+                                Counters &cnt) {
     static_assert(SN <= 2048, "32 groups of at most 64 vertices");
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = lane_id();
@@ -515,7 +519,10 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
     int *r = sm.r;
     int *rps = sm.u.rp;
     u32 *gmax = reinterpret_cast<u32 *>(sm.head);
-    for (int v = lane; v <= n; v += 32) rps[v] = A.g.rp[v];
+    for (int v = lane; v <= n; v += 32) {
+        rps[v] = A.g.rp[v];
+        if (v < n) joinx[v] = -1;
+    }
     gmax[lane] = 0u;
     __syncwarp();
     long long L = ld_volatile_i64(&A.st->lam);
@@ -548,27 +555,21 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
         cnt.verts++;
         cnt.arcs += a1 - a0;
         __syncwarp();
-        int xh = p;
         for (int i0 = a0; i0 < a1; i0 += 32) {
             const int i = i0 + lane;
-            const int2 e = i < a1 ? A.g.adj[i] : make_int2(0, 0);
-            const int y = e.x;
-            bool join = false;
             if (i < a1) {
+                const int2 e = A.g.adj[i];
+                const int y = e.x;
                 const int ro = r[y];
                 if (ro != kDone) {
                     const int rn = sat_add(ro, e.y);
                     r[y] = rn;
                     // a certificate min(r, C) only vouches for bounds <= C
-                    join = ro < Lj && Lj <= rn;
+                    if (ro < Lj && Lj <= rn) joinx[y] = p;
                     const int ko = ro == 0 ? 0 : (ro < C ? ro : C) + 1, kn = (rn < C ? rn : C) + 1;
                     if (ko != kn) atomicMax(&gmax[y >> lgB], ((u32)kn << 5) | (u32)(31 - (y >> lgB)));
                 }
             }
-            int rt = INT_MAX;
-            if (join && uf_union_root(A.par, xh, y, &rt)) cnt.unions++;
-            rt = __reduce_min_sync(kAll, rt);
-            if (rt != INT_MAX) xh = rt;
         }
         __syncwarp();
         // the next pop: best group, then its best vertex
@@ -598,6 +599,10 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
         A.rec_alpha[1] = best;
         A.rec_len[1] = best_len;
     }
+    __syncwarp();
+    for (int y = lane; y < n; y += 32)
+        if (joinx[y] >= 0 && uf_union(A.par, joinx[y], y)) cnt.unions++;
+    __syncwarp();
 }
 
 // one full capped CAPFOREST scan of the current graph (Alg. 3)
@@ -620,7 +625,7 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
     if (in_smem && n <= 256 && C <= 63 && !fifo) {
         warp_scan_bits<SN>(A, sm, n, C, start, cnt);
     } else if (in_smem && !fifo && C < (1 << 25)) {
-        warp_scan_dense<SN>(A, sm, n, C, start, cnt);
+        warp_scan_dense<SN>(A, sm, n, C, start, S.rg, cnt);
     } else if (in_smem) {
         BucketQ<unsigned short, kBNB> q;
         q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.u.q.eslot; q.enext = sm.u.q.enext;
@@ -739,19 +744,23 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     // self-loop, positive weights, neighbours in range) is copied into A in
     // one arc-parallel pass: each arc's row by binary search in the offsets
     // (staged on chip when they fit), the degrees by a segmented sum over
-    // the lanes of a row.  The same pass checks symmetry: every downward arc
-    // (v < u) finds its mirror with the same weight by binary search in row
-    // v, and the upward and downward arcs are equally many (rows hold no
-    // duplicates, so the mirror map is then a bijection).  Each lane carries
-    // kCU arcs at once so that the searches' dependent loads overlap.  Other
-    // input takes the general path below (drop, sort, merge, symmetry check).
+    // the lanes of a row.  The same pass checks symmetry in row order: the
+    // downward arcs (u -> v, v < u) that reach v, met in increasing u, must
+    // match the entries of row v above v one by one (a cursor per row,
+    // starting at the row's first entry above v), with equal weights, and
+    // every cursor must end at its row's end; that pairs every arc with its
+    // mirror.  The mirror loads of a chunk are independent of one another.
+    // Each lane carries kCU arcs at once.  Other input takes the general
+    // path below (drop, sort, merge, symmetry check).
     constexpr int kCU = 4;
     const int m_raw = __ldg(rp_in + n0);
     const bool rp_on_chip = n0 < SN;
+    int *cur = rp_on_chip ? sm.u.rp : S.cnt;
     for (int v = lane; v <= n0; v += 32) {
         const int r = __ldg(rp_in + v);
         S.rpA[v] = r;
         if (rp_on_chip) sm.r[v] = r;
+        if (v > 0) cur[v - 1] = r;  // no entry above v-1 seen yet: the row's end
     }
     for (int v = lane; v < n0; v += 32) S.deg[v] = 0;
     __syncwarp();
@@ -760,7 +769,6 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     while (top_row * 2 <= n0 - 1) top_row *= 2;
     bool canon = m_raw >= 0;
     bool sym_ok = true;
-    int ups = 0, downs = 0;
     for (int i0 = 0; i0 < m_raw && canon; i0 += 32 * kCU) {
         int u[kCU], v[kCU], c[kCU];
 #pragma unroll
@@ -780,52 +788,43 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
             }
         }
         bool ok = true;
-        int base[kCU], len[kCU], cnt[kCU];
-        bool down[kCU];
-        unsigned maxlen = 0;
 #pragma unroll
         for (int j = 0; j < kCU; ++j) {
             const int i = i0 + 32 * j + lane;
             int pv = __shfl_up_sync(0xffffffffu, v[j], 1);  // the previous arc's neighbour
             const int last = __shfl_sync(0xffffffffu, v[(j + kCU - 1) % kCU], 31);
             if (lane == 0) pv = j > 0 ? last : prev0;
-            down[j] = false;
-            len[j] = 0;
-            base[j] = 0;
-            cnt[j] = 0;
             if (u[j] >= 0) {
                 const bool row_first = i == rps[u[j]];
-                const bool okj = v[j] >= 0 && v[j] < n0 && v[j] != u[j] && c[j] > 0 && (row_first || pv < v[j]);
-                ok = ok && okj;
+                ok = ok && v[j] >= 0 && v[j] < n0 && v[j] != u[j] && c[j] > 0 && (row_first || pv < v[j]);
                 S.srcA[i] = u[j];
                 S.adjA[i] = make_int2(v[j], c[j]);
-                if (okj && v[j] < u[j]) {
-                    ++downs;
-                    down[j] = true;
-                    base[j] = rps[v[j]];
-                    len[j] = rps[v[j] + 1] - base[j];
-                    maxlen = max(maxlen, (unsigned)len[j]);
-                } else if (okj) {
-                    ++ups;
-                }
+                if (v[j] > u[j] && (row_first || pv < u[j])) cur[u[j]] = i;  // row u's first entry above u
             }
         }
-        // mirror of each downward arc: the entries of row v below u, counted
-        // by a branch-free binary search whose steps all lanes share
-        maxlen = __reduce_max_sync(0xffffffffu, maxlen);
-        int top_len = maxlen ? 1 : 0;
-        while (top_len && top_len * 2 <= (int)maxlen) top_len *= 2;
-        for (int step = top_len; step > 0; step >>= 1) {
+        __syncwarp();
+        // each downward arc takes the next entry above v in row v; lanes
+        // meeting the same v are in row order, ranked by match_any
+        int at[kCU], mv[kCU], mw[kCU];
 #pragma unroll
-            for (int j = 0; j < kCU; ++j)
-                if (cnt[j] + step <= len[j] && col_in[base[j] + cnt[j] + step - 1] < u[j]) cnt[j] += step;
+        for (int j = 0; j < kCU; ++j) {
+            const bool dn = u[j] >= 0 && v[j] >= 0 && v[j] < u[j];
+            const unsigned peers = __match_any_sync(0xffffffffu, dn ? v[j] : -1 - lane);
+            at[j] = -1;
+            if (dn) at[j] = cur[v[j]] + __popc(peers & ((1u << lane) - 1u));
+            __syncwarp();
+            if (dn && (peers >> lane) == 1u) cur[v[j]] = at[j] + 1;
+            __syncwarp();
+            mv[j] = -1;
+            mw[j] = 0;
+            if (dn && at[j] < rps[v[j] + 1]) {
+                mv[j] = col_in[at[j]];
+                mw[j] = w_in[at[j]];
+            }
         }
 #pragma unroll
         for (int j = 0; j < kCU; ++j) {
-            if (down[j]) {
-                const int at = base[j] + cnt[j];
-                if (cnt[j] >= len[j] || col_in[at] != u[j] || w_in[at] != c[j]) sym_ok = false;
-            }
+            if (at[j] >= 0 && (mv[j] != u[j] || mw[j] != c[j])) sym_ok = false;
             // the lanes of one row add their weights toward its first lane
             long long cs = c[j];
             const int pu = __shfl_up_sync(0xffffffffu, u[j], 1);
@@ -842,7 +841,9 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     }
     if (canon) {
         arcs = m_raw;
-        if (!__all_sync(0xffffffffu, sym_ok) || warp_sum_ll(ups) != warp_sum_ll(downs)) err = MC_EINVAL;
+        for (int x = lane; x < n0; x += 32)
+            if (cur[x] != rps[x + 1]) sym_ok = false;  // an entry above x with no downward arc
+        if (!__all_sync(0xffffffffu, sym_ok)) err = MC_EINVAL;
         __syncwarp();
     }
 
