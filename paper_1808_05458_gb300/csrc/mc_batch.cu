@@ -531,47 +531,70 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
     int nS = 0, best_len = 0;
     bool alpha_ok = true;
     cnt.scans++;
-    int p = start;
-    while (p >= 0 && nS < n) {
-        const int a0 = rps[p], a1 = rps[p + 1];
-        const int rx = r[p];
-        const long long dx = A.g.deg[p];
-        __syncwarp();
-        if (lane == 0) {
-            r[p] = kDone;
-            A.T[p] = 1;
-            A.order[p] = nS;
-        }
-        ++nS;
-        if (rx >= kSat) alpha_ok = false;
-        alpha += dx - 2LL * rx;
-        if (alpha_ok && nS < n && alpha < L) {
-            if (lane == 0) atomicMin(&A.st->lam, alpha);
-            best = alpha;
-            best_len = nS;
-            L = alpha;
-            Lj = L <= C ? (int)L : INT_MAX;
-        }
-        cnt.verts++;
-        cnt.arcs += a1 - a0;
-        __syncwarp();
-        for (int i0 = a0; i0 < a1; i0 += 32) {
-            const int i = i0 + lane;
-            if (i < a1) {
-                const int2 e = A.g.adj[i];
-                const int y = e.x;
-                const int ro = r[y];
-                if (ro != kDone) {
-                    const int rn = sat_add(ro, e.y);
-                    r[y] = rn;
-                    // a certificate min(r, C) only vouches for bounds <= C
-                    if (ro < Lj && Lj <= rn) joinx[y] = p;
-                    const int ko = ro == 0 ? 0 : (ro < C ? ro : C) + 1, kn = (rn < C ? rn : C) + 1;
-                    if (ko != kn) atomicMax(&gmax[y >> lgB], ((u32)kn << 5) | (u32)(31 - (y >> lgB)));
-                }
+    // the vertices popped next, in order: one, or up to kCap at the cap
+    constexpr int kCap = 4;
+    int nb = 1;
+    int bx[kCap] = {start, 0, 0, 0};
+    while (nb > 0) {
+        // every row of the batch starts its loads before the first pop
+        int a0[kCap], a1[kCap];
+        long long dxs[kCap];
+        int2 e0[kCap];
+#pragma unroll
+        for (int t = 0; t < kCap; ++t) {
+            a0[t] = a1[t] = 0;
+            dxs[t] = 0;
+            e0[t] = make_int2(0, 0);
+            if (t < nb) {
+                a0[t] = rps[bx[t]];
+                a1[t] = rps[bx[t] + 1];
+                dxs[t] = A.g.deg[bx[t]];
+                if (lane < a1[t] - a0[t]) e0[t] = A.g.adj[a0[t] + lane];
             }
         }
-        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kCap; ++t) {
+            if (t >= nb) break;
+            const int p = bx[t];
+            const int rx = r[p];
+            __syncwarp();
+            if (lane == 0) {
+                r[p] = kDone;
+                A.T[p] = 1;
+                A.order[p] = nS;
+            }
+            ++nS;
+            if (rx >= kSat) alpha_ok = false;
+            alpha += dxs[t] - 2LL * rx;
+            if (alpha_ok && nS < n && alpha < L) {
+                if (lane == 0) atomicMin(&A.st->lam, alpha);
+                best = alpha;
+                best_len = nS;
+                L = alpha;
+                Lj = L <= C ? (int)L : INT_MAX;
+            }
+            cnt.verts++;
+            cnt.arcs += a1[t] - a0[t];
+            __syncwarp();
+            for (int i0 = a0[t]; i0 < a1[t]; i0 += 32) {
+                const int i = i0 + lane;
+                if (i < a1[t]) {
+                    const int2 e = i0 == a0[t] ? e0[t] : A.g.adj[i];
+                    const int y = e.x;
+                    const int ro = r[y];
+                    if (ro != kDone) {
+                        const int rn = sat_add(ro, e.y);
+                        r[y] = rn;
+                        // a certificate min(r, C) only vouches for bounds <= C
+                        if (ro < Lj && Lj <= rn) joinx[y] = p;
+                        const int ko = ro == 0 ? 0 : (ro < C ? ro : C) + 1, kn = (rn < C ? rn : C) + 1;
+                        if (ko != kn) atomicMax(&gmax[y >> lgB], ((u32)kn << 5) | (u32)(31 - (y >> lgB)));
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (nS >= n) break;
         // the next pop: best group, then its best vertex
         const u32 top = __reduce_max_sync(kAll, gmax[lane]);
         if (top == 0u) break;
@@ -588,8 +611,36 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
         }
         const u32 m = __reduce_max_sync(kAll, k0 > k1 ? k0 : k1);
         if (m == 0u) break;  // a group entry always has a reached member
-        p = (g << lgB) + 63 - (int)(m & 63u);
-        const u32 x0 = k0 == m ? 0u : k0, x1 = k1 == m ? 0u : k1;
+        u32 x0, x1;
+        const u32 capk = (u32)C + 1u;
+        if ((m >> 6) == capk) {
+            // members at the cap go up to kCap at a time, smallest first: no
+            // key passes the cap, so each is still a largest key at its pop
+            // (a later one's r takes the earlier rows' weights as it would
+            // one pop at a time)
+            const unsigned s0 = __ballot_sync(kAll, (k0 >> 6) == capk), s1 = __ballot_sync(kAll, (k1 >> 6) == capk);
+            unsigned t0 = s0, t1 = s1;
+            nb = 0;
+#pragma unroll
+            for (int t = 0; t < kCap; ++t) {
+                if (t0) {
+                    bx[t] = (g << lgB) + __ffs(t0) - 1;
+                    t0 &= t0 - 1u;
+                    nb = t + 1;
+                } else if (t1) {
+                    bx[t] = (g << lgB) + 32 + __ffs(t1) - 1;
+                    t1 &= t1 - 1u;
+                    nb = t + 1;
+                }
+            }
+            x0 = (((s0 & ~t0) >> lane) & 1u) ? 0u : k0;
+            x1 = (((s1 & ~t1) >> lane) & 1u) ? 0u : k1;
+        } else {
+            nb = 1;
+            bx[0] = (g << lgB) + 63 - (int)(m & 63u);
+            x0 = k0 == m ? 0u : k0;
+            x1 = k1 == m ? 0u : k1;
+        }
         const u32 m2 = __reduce_max_sync(kAll, x0 > x1 ? x0 : x1);
         __syncwarp();
         if (lane == 0) gmax[g] = m2 ? ((m2 >> 6) << 5) | (u32)(31 - g) : 0u;
@@ -661,21 +712,67 @@ __device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arc
         __syncwarp();
         long long un = 0;
         // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
+        // (kPU arcs or vertices a lane at a time, so that their loads overlap)
         if (pr_level >= 1) {
-            for (long long i = lane; i < arcs; i += 32) {
-                const int u = srcA[i];
-                const int2 e = adjA[i];
-                if (u >= e.x) continue;
-                const long long c = e.y, du = S.deg[u], dv = S.deg[e.x];
-                const bool ok = c >= lam || (pr_level >= 2 && 2 * c > (du < dv ? du : dv));
-                if (ok && uf_union(S.par, u, e.x)) ++un;
+            constexpr int kPU = 4;
+            for (long long i0 = 0; i0 < arcs; i0 += 32 * kPU) {
+                int uu[kPU];
+                int2 ee[kPU];
+                long long du[kPU], dv[kPU];
+#pragma unroll
+                for (int j = 0; j < kPU; ++j) {
+                    const long long i = i0 + 32 * j + lane;
+                    uu[j] = -1;
+                    ee[j] = make_int2(-1, 0);
+                    if (i < arcs) {
+                        uu[j] = srcA[i];
+                        ee[j] = adjA[i];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kPU; ++j) {
+                    du[j] = dv[j] = 0;
+                    if (pr_level >= 2 && uu[j] >= 0 && uu[j] < ee[j].x && ee[j].y < lam) {
+                        du[j] = S.deg[uu[j]];
+                        dv[j] = S.deg[ee[j].x];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kPU; ++j) {
+                    if (uu[j] < 0 || uu[j] >= ee[j].x) continue;
+                    const long long c = ee[j].y;
+                    const bool ok = c >= lam || (pr_level >= 2 && 2 * c > (du[j] < dv[j] ? du[j] : dv[j]));
+                    if (ok && uf_union(S.par, uu[j], ee[j].x)) ++un;
+                }
             }
             if (pr_level >= 2) {
-                for (int u = lane; u < n; u += 32) {
-                    const int a = rpA[u];
-                    if (rpA[u + 1] - a != 2) continue;
-                    const int2 e0 = adjA[a], e1 = adjA[a + 1];
-                    if (e0.y == e1.y && uf_union(S.par, u, e0.x < e1.x ? e0.x : e1.x)) ++un;
+                for (int u0 = 0; u0 < n; u0 += 32 * kPU) {
+                    int a[kPU], d[kPU];
+                    int2 f0[kPU], f1[kPU];
+#pragma unroll
+                    for (int j = 0; j < kPU; ++j) {
+                        const int u = u0 + 32 * j + lane;
+                        a[j] = d[j] = 0;
+                        if (u < n) {
+                            a[j] = rpA[u];
+                            d[j] = rpA[u + 1] - a[j];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kPU; ++j) {
+                        f0[j] = f1[j] = make_int2(0, 0);
+                        if (d[j] == 2) {
+                            f0[j] = adjA[a[j]];
+                            f1[j] = adjA[a[j] + 1];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kPU; ++j) {
+                        const int u = u0 + 32 * j + lane;
+                        if (d[j] == 2 && f0[j].y == f1[j].y &&
+                            uf_union(S.par, u, f0[j].x < f1[j].x ? f0[j].x : f1[j].x))
+                            ++un;
+                    }
                 }
             }
             __syncwarp();
