@@ -38,7 +38,14 @@ struct WarpSmem {
             unsigned short eslot[SN + SN / 2];
             unsigned short enext[SN + SN / 2];
         } q;             // the bucket queue's entry pool
-        int rp[SN + 1];  // or the row offsets, for the dense on-chip scan
+        struct {
+            int rp[SN + 1];                // the row offsets, for the dense on-chip scan
+            unsigned short par[SN - 2];    // the union-find of a graph of <= SN - 2 vertices
+        } s;             // or the round's on-chip arrays
+        struct {
+            int acc[SN];               // merged weights by target
+            unsigned short lab[SN];    // the new labels of the n vertices
+        } c;             // or the on-chip contraction's arrays
     } u;
     int head[kBNB];
     int tail[kBNB];
@@ -274,6 +281,172 @@ __device__ long long warp_contract(const int *in_src, const int2 *in_adj, long l
     return out;
 }
 
+// Contraction of a graph on chip (n <= SN vertices, nc < n): the steps of
+// warp_contract with the per-vertex arrays in shared memory -- 16-bit labels,
+// the counts, then cursors, then first positions of the merge (in r), and
+// the merged weights -- so that only the arcs travel through global memory.
+// The count and scatter passes load four chunks of arcs a lane at a time, the
+// merge reads row bounds 32 rows at a time, and a row of at most 32 arcs is
+// merged in registers with the next such row's load already in flight.
+// Merged weights saturate at `clamp` from the first addition on.
+template <int SN>
+__device__ long long warp_contract_chip(const int *in_src, const int2 *in_adj, long long m, const int *lab_g,
+                                        int n, int nc, long long clamp, int *tmp_rp, int2 *tmp_adj, int *rp,
+                                        int *src, int2 *adj, i64 *deg, WarpSmem<SN> &sm, int *ovf) {
+    constexpr int kU = 4;
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = lane_id();
+    int *mark = sm.r;
+    int *acc = sm.u.c.acc;
+    unsigned short *lab = sm.u.c.lab;
+    for (int v = lane; v < n; v += 32) lab[v] = (unsigned short)lab_g[v];
+    for (int a = lane; a <= nc; a += 32) mark[a] = 0;
+    __syncwarp();
+    for (long long i0 = 0; i0 < m; i0 += 32 * kU) {
+        int s[kU], t[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            const long long i = i0 + 32 * j + lane;
+            s[j] = t[j] = 0;
+            if (i < m) {
+                s[j] = in_src[i];
+                t[j] = in_adj[i].x;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            const int a = lab[s[j]], b = lab[t[j]];
+            if (i0 + 32 * j + lane < m && a != b) atomicAdd(&mark[a], 1);
+        }
+    }
+    __syncwarp();
+    warp_excl_scan(mark, mark, nc);  // in place: each entry is read and written by its own lane
+    for (int a = lane; a <= nc; a += 32) tmp_rp[a] = mark[a];
+    __syncwarp();
+    // stable scatter: the lanes of a chunk meeting the same row ranked by match_any
+    for (long long i0 = 0; i0 < m; i0 += 32 * kU) {
+        int s[kU];
+        int2 e[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            const long long i = i0 + 32 * j + lane;
+            s[j] = 0;
+            e[j] = make_int2(0, 0);
+            if (i < m) {
+                s[j] = in_src[i];
+                e[j] = in_adj[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            int a = -1 - lane, b = 0;
+            if (i0 + 32 * j + lane < m) {
+                a = lab[s[j]];
+                b = lab[e[j].x];
+                if (a == b) a = -1 - lane;
+            }
+            const unsigned peers = __match_any_sync(kAll, a);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            int base = 0;
+            if (a >= 0) base = mark[a];
+            __syncwarp();
+            if (a >= 0) {
+                tmp_adj[base + rank] = make_int2(b, e[j].y);
+                if (rank == 0) mark[a] = base + __popc(peers);
+            }
+            __syncwarp();
+        }
+    }
+    // merge parallel arcs row by row: the first occurrence keeps the arc
+    for (int a = lane; a < nc; a += 32) mark[a] = INT_MAX;
+    __syncwarp();
+    long long out = 0;
+    for (int a0 = 0; a0 < nc; a0 += 32) {
+        const int rows = nc - a0 < 32 ? nc - a0 : 32;
+        const int bl = lane <= rows ? tmp_rp[a0 + lane] : 0;       // bounds of rows a0 .. a0 + 31
+        const int bend = rows == 32 ? tmp_rp[a0 + 32] : 0;         // the end of row a0 + 31
+        int lo = __shfl_sync(kAll, bl, 0), hi = __shfl_sync(kAll, bl, 1);
+        int2 xn = make_int2(0, 0);
+        if (hi - lo <= 32 && lane < hi - lo) xn = tmp_adj[lo + lane];
+        for (int k = 0; k < rows; ++k) {
+            const int a = a0 + k;
+            const int2 x = xn;
+            // the next row's bounds, and its arcs if it is short
+            const int nhi_l = __shfl_sync(kAll, bl, (k + 2) & 31);
+            const int nlo = hi, nhi = k + 2 <= 31 ? nhi_l : (k + 2 == 32 ? bend : nlo);
+            if (k + 1 < rows && nhi - nlo <= 32 && lane < nhi - nlo) xn = tmp_adj[nlo + lane];
+            if (lane == 0) rp[a] = (int)out;
+            long long dsum;
+            if (hi - lo <= 32) {
+                const bool v = lane < hi - lo;
+                if (v) {
+                    atomicMin(&mark[x.x], lane);
+                    acc[x.x] = 0;
+                }
+                __syncwarp();
+                if (v) add_clamped(&acc[x.x], x.y, clamp, ovf);
+                __syncwarp();
+                const bool keep = v && mark[x.x] == lane;
+                const int wv = keep ? acc[x.x] : 0;
+                const unsigned kb = __ballot_sync(kAll, keep);
+                if (keep) {
+                    const long long pos = out + __popc(kb & ((1u << lane) - 1u));
+                    adj[pos] = make_int2(x.x, wv);
+                    src[pos] = a;
+                }
+                out += __popc(kb);
+                // weights below 2^31: the two 16-bit halves sum without carry-out
+                dsum = (long long)__reduce_add_sync(kAll, (unsigned)wv >> 16) * 65536 +
+                       (long long)__reduce_add_sync(kAll, (unsigned)wv & 0xFFFFu);
+                __syncwarp();
+                if (v) mark[x.x] = INT_MAX;
+            } else {
+                for (int e = lo + lane; e < hi; e += 32) {
+                    const int2 y = tmp_adj[e];
+                    atomicMin(&mark[y.x], e);
+                    acc[y.x] = 0;
+                }
+                __syncwarp();
+                for (int e = lo + lane; e < hi; e += 32) {
+                    const int2 y = tmp_adj[e];
+                    add_clamped(&acc[y.x], y.y, clamp, ovf);
+                }
+                __syncwarp();
+                long long ds = 0;
+                for (int e0 = lo; e0 < hi; e0 += 32) {
+                    const int e = e0 + lane;
+                    bool keep = false;
+                    int2 y = make_int2(0, 0);
+                    if (e < hi) {
+                        y = tmp_adj[e];
+                        keep = mark[y.x] == e;
+                    }
+                    const int wv = keep ? acc[y.x] : 0;
+                    const unsigned kb = __ballot_sync(kAll, keep);
+                    if (keep) {
+                        const long long pos = out + __popc(kb & ((1u << lane) - 1u));
+                        adj[pos] = make_int2(y.x, wv);
+                        src[pos] = a;
+                    }
+                    out += __popc(kb);
+                    ds += wv;
+                }
+                dsum = warp_sum_ll(ds);
+                __syncwarp();
+                for (int e = lo + lane; e < hi; e += 32) mark[tmp_adj[e].x] = INT_MAX;
+            }
+            if (lane == 0) deg[a] = dsum;
+            __syncwarp();
+            lo = nlo;
+            hi = nhi;
+            if (k + 1 < rows && (hi - lo > 32)) xn = make_int2(0, 0);
+        }
+    }
+    if (lane == 0) rp[nc] = (int)out;
+    __syncwarp();
+    return out;
+}
+
 // Stable transpose of the arcs (src[i] -> adj[i].x, weight adj[i].y), i in
 // [0, m), over n vertices: row v of the result lists (u, c) for every arc
 // u -> v in the input's index order; out_src[j] = v.  An input whose arcs
@@ -359,10 +532,56 @@ __device__ bool warp_symmetric(const int *rp, const int *src, const int2 *adj, l
 
 // flatten the union-find par[0..n) into root[] and number the blocks in
 // lab[] (order of the smallest member); returns the block count
-__device__ int warp_relabel(int *par, int *root, int *lab, int *cnt, int n) {
+// Union-find over 32-bit parents in global memory or 16-bit parents on chip
+// (graphs of at most 65535 vertices): the parent of a vertex is always below
+// it, a union links the larger root under the smaller by CAS, and a find
+// halves the path it walks (only ever shortening paths to ancestors).
+template <class P>
+__device__ __forceinline__ int wuf_find(P *par, int x) {
+    volatile P *p = par;
+    while (true) {
+        const int px = p[x];
+        if (px == x) return x;
+        const int gx = p[px];
+        if (gx == px) return px;
+        p[x] = (P)gx;
+        x = gx;
+    }
+}
+
+template <class P>
+__device__ __forceinline__ bool wuf_union(P *par, int a, int b) {
+    while (true) {
+        a = wuf_find(par, a);
+        b = wuf_find(par, b);
+        if (a == b) return false;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if ((int)atomicCAS(&par[b], (P)b, (P)a) == b) return true;
+    }
+}
+
+// the unions a scan recorded (joinx[y] = the vertex whose pop made y join,
+// -1 if none), applied after the scan; 16-bit parents when par16 is set
+__device__ __forceinline__ void apply_joins(const int *joinx, int n, int *par32, unsigned short *par16,
+                                            Counters &cnt) {
+    const int lane = lane_id();
+    __syncwarp();
+    for (int y = lane; y < n; y += 32) {
+        const int x = joinx[y];
+        if (x >= 0 && (par16 ? wuf_union(par16, x, y) : wuf_union(par32, x, y))) cnt.unions++;
+    }
+    __syncwarp();
+}
+
+template <class P>
+__device__ int warp_relabel(P *par, int *root, int *lab, int *cnt, int n) {
     const int lane = lane_id();
     for (int v = lane; v < n; v += 32) {
-        const int r = uf_find(par, v);
+        const int r = wuf_find(par, v);
         root[v] = r;
         cnt[v] = r == v;
     }
@@ -397,14 +616,17 @@ __device__ void warp_side_bits(u32 *bits, int n0, F f) {
 // move (keys only rise): one warp reduction per 32 arcs, no second search.
 // Measured on the tail of RHG 2^20 (71 vertices): the list-queue scan took
 // about 2000 cycles per pop.
+// Joins are recorded in joinx and applied after the scan (apply_joins).
 template <int SN>
-__device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, Counters &cnt) {
+__device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, int *joinx,
+                               unsigned short *par16, Counters &cnt) {
     static_assert(2 * kBNB >= 64 * 8, "bitmaps of 64 keys fit the head and tail arrays");
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = lane_id();
     u32 *b0 = reinterpret_cast<u32 *>(sm.head);  // (C + 1) x 8 words
     int *r = sm.r;
     for (int i = lane; i < (C + 1) * 8; i += 32) b0[i] = 0;
+    for (int v = lane; v < n; v += 32) joinx[v] = -1;
     __syncwarp();
     if (lane == 0) b0[start >> 5] = 1u << (start & 31);  // key 0
     __syncwarp();
@@ -452,20 +674,18 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
         const unsigned qe = search();  // before p's moves change the bitmaps
         __syncwarp();
         unsigned be = qe;
-        int xh = p;
         for (int i0 = a0; i0 < a1; i0 += 32) {
             const int i = i0 + lane;
             const int2 e = i < a1 ? A.g.adj[i] : make_int2(0, 0);
             const int y = e.x;
             unsigned me = 0u;
-            bool join = false;
             if (i < a1) {
                 const int ro = r[y];
                 if (ro != kDone) {
                     const int rn = sat_add(ro, e.y);
                     r[y] = rn;
                     // a certificate min(r, C) only vouches for bounds <= C
-                    join = ro < Lj && Lj <= rn;
+                    if (ro < Lj && Lj <= rn) joinx[y] = p;
                     const int ko = ro == 0 ? -1 : (ro < C ? ro : C), kn = rn < C ? rn : C;
                     if (ko != kn) {
                         const u32 bit = 1u << (y & 31);
@@ -475,10 +695,6 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
                     }
                 }
             }
-            int rt = INT_MAX;
-            if (join && uf_union_root(A.par, xh, y, &rt)) cnt.unions++;
-            rt = __reduce_min_sync(kAll, rt);
-            if (rt != INT_MAX) xh = rt;
             me = __reduce_max_sync(kAll, me);
             be = me > be ? me : be;
         }
@@ -491,6 +707,7 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
         A.rec_alpha[1] = best;
         A.rec_len[1] = best_len;
     }
+    apply_joins(joinx, n, A.par, par16, cnt);
 }
 
 // One full capped CAPFOREST scan (Alg. 3) of a graph held on chip (n <= SN
@@ -509,7 +726,7 @@ __device__ void warp_scan_bits(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C
 // scan in one lane-parallel pass, off the pops' chain of latencies.
 template <int SN>
 __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int C, int start, int *joinx,
-                                Counters &cnt) {
+                                unsigned short *par16, Counters &cnt) {
     static_assert(SN <= 2048, "32 groups of at most 64 vertices");
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = lane_id();
@@ -517,7 +734,7 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
     while ((32 << lgB) < n) ++lgB;
     const int B = 1 << lgB;
     int *r = sm.r;
-    int *rps = sm.u.rp;
+    int *rps = sm.u.s.rp;
     u32 *gmax = reinterpret_cast<u32 *>(sm.head);
     for (int v = lane; v <= n; v += 32) {
         rps[v] = A.g.rp[v];
@@ -650,16 +867,22 @@ __device__ void warp_scan_dense(const ScanArgs &A, WarpSmem<SN> &sm, int n, int 
         A.rec_alpha[1] = best;
         A.rec_len[1] = best_len;
     }
-    __syncwarp();
-    for (int y = lane; y < n; y += 32)
-        if (joinx[y] >= 0 && uf_union(A.par, joinx[y], y)) cnt.unions++;
-    __syncwarp();
+    apply_joins(joinx, n, A.par, par16, cnt);
 }
 
-// one full capped CAPFOREST scan of the current graph (Alg. 3)
+// A round whose scan takes the bitmap or the dense queue (graph on chip, cap
+// below 2^25, no FIFO order) keeps its union-find on chip, in 16-bit parents
+// beside the staged row offsets; other rounds keep it in global memory.
+template <int SN>
+__device__ __forceinline__ bool round_on_chip(int n, long long lam, int fifo) {
+    return n <= SN - 2 && !fifo && lam < (1 << 25);
+}
+
+// one full capped CAPFOREST scan of the current graph (Alg. 3); par16 (only
+// with round_on_chip) holds the union-find instead of A.par
 template <int SN>
 __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, int n, long long arcs,
-                               long long lam, int start, int fifo, Counters &cnt) {
+                               long long lam, int start, int fifo, unsigned short *par16, Counters &cnt) {
     const int lane = lane_id();
     const bool in_smem = n <= SN;
     int *r = in_smem ? sm.r : S.rg;
@@ -674,9 +897,9 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
     __syncwarp();
     const int C = (int)(lam < (long long)0x7FFFFFFD ? lam : (long long)0x7FFFFFFD);
     if (in_smem && n <= 256 && C <= 63 && !fifo) {
-        warp_scan_bits<SN>(A, sm, n, C, start, cnt);
+        warp_scan_bits<SN>(A, sm, n, C, start, S.rg, par16, cnt);
     } else if (in_smem && !fifo && C < (1 << 25)) {
-        warp_scan_dense<SN>(A, sm, n, C, start, S.rg, cnt);
+        warp_scan_dense<SN>(A, sm, n, C, start, S.rg, par16, cnt);
     } else if (in_smem) {
         BucketQ<unsigned short, kBNB> q;
         q.head = sm.head; q.tail = sm.tail; q.bits = sm.bits; q.eslot = sm.u.q.eslot; q.enext = sm.u.q.enext;
@@ -691,6 +914,80 @@ __device__ void warp_full_scan(const ScanArgs &A, WarpSmem<SN> &sm, Scratch &S, 
         scan_one<DenseTable, BucketQ<int, kBNB>, false, true>(A, tab, q, start, 1, cnt);
     }
     __syncwarp();
+}
+
+// Padberg-Rinaldi PR1/PR2 (Sec. 2.2) and the degree-2 tie rule on the graph
+// (rp, src, adj, deg) against lambda-hat `lam`: the unions go into par; kPU
+// arcs or vertices a lane at a time, so that their loads overlap.  Returns
+// this lane's count of successful unions.
+template <class P>
+__device__ long long pr_unions(P *par, const int *rpA, const int *srcA, const int2 *adjA, const i64 *deg, int n,
+                               long long arcs, long long lam, int pr_level) {
+    const int lane = lane_id();
+    long long un = 0;
+    constexpr int kPU = 4;
+    for (long long i0 = 0; i0 < arcs; i0 += 32 * kPU) {
+        int uu[kPU];
+        int2 ee[kPU];
+        long long du[kPU], dv[kPU];
+#pragma unroll
+        for (int j = 0; j < kPU; ++j) {
+            const long long i = i0 + 32 * j + lane;
+            uu[j] = -1;
+            ee[j] = make_int2(-1, 0);
+            if (i < arcs) {
+                uu[j] = srcA[i];
+                ee[j] = adjA[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPU; ++j) {
+            du[j] = dv[j] = 0;
+            if (pr_level >= 2 && uu[j] >= 0 && uu[j] < ee[j].x && ee[j].y < lam) {
+                du[j] = deg[uu[j]];
+                dv[j] = deg[ee[j].x];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPU; ++j) {
+            if (uu[j] < 0 || uu[j] >= ee[j].x) continue;
+            const long long c = ee[j].y;
+            const bool ok = c >= lam || (pr_level >= 2 && 2 * c > (du[j] < dv[j] ? du[j] : dv[j]));
+            if (ok && wuf_union(par, uu[j], ee[j].x)) ++un;
+        }
+    }
+    if (pr_level >= 2) {
+        for (int u0 = 0; u0 < n; u0 += 32 * kPU) {
+            int a[kPU], d[kPU];
+            int2 f0[kPU], f1[kPU];
+#pragma unroll
+            for (int j = 0; j < kPU; ++j) {
+                const int u = u0 + 32 * j + lane;
+                a[j] = d[j] = 0;
+                if (u < n) {
+                    a[j] = rpA[u];
+                    d[j] = rpA[u + 1] - a[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kPU; ++j) {
+                f0[j] = f1[j] = make_int2(0, 0);
+                if (d[j] == 2) {
+                    f0[j] = adjA[a[j]];
+                    f1[j] = adjA[a[j] + 1];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kPU; ++j) {
+                const int u = u0 + 32 * j + lane;
+                if (d[j] == 2 && f0[j].y == f1[j].y &&
+                    wuf_union(par, u, f0[j].x < f1[j].x ? f0[j].x : f1[j].x))
+                    ++un;
+            }
+        }
+    }
+    __syncwarp();
+    return un;
 }
 
 // Alg. 2's rounds on the graph in the A buffers of S (n vertices, `arcs`
@@ -708,75 +1005,18 @@ __device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arc
     int round = 0, guard = 0;
     while (!err && n >= 2 && lam > 0) {
         if (++guard > 4 * n0 + 16) { err = MC_EINTERNAL; break; }
-        for (int v = lane; v < n; v += 32) S.par[v] = v;
+        const bool chip = round_on_chip<SN>(n, lam, fifo);
+        unsigned short *par16 = chip ? sm.u.s.par : nullptr;
+        for (int v = lane; v < n; v += 32) {
+            if (chip) par16[v] = (unsigned short)v;
+            else S.par[v] = v;
+        }
         __syncwarp();
         long long un = 0;
         // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
-        // (kPU arcs or vertices a lane at a time, so that their loads overlap)
-        if (pr_level >= 1) {
-            constexpr int kPU = 4;
-            for (long long i0 = 0; i0 < arcs; i0 += 32 * kPU) {
-                int uu[kPU];
-                int2 ee[kPU];
-                long long du[kPU], dv[kPU];
-#pragma unroll
-                for (int j = 0; j < kPU; ++j) {
-                    const long long i = i0 + 32 * j + lane;
-                    uu[j] = -1;
-                    ee[j] = make_int2(-1, 0);
-                    if (i < arcs) {
-                        uu[j] = srcA[i];
-                        ee[j] = adjA[i];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kPU; ++j) {
-                    du[j] = dv[j] = 0;
-                    if (pr_level >= 2 && uu[j] >= 0 && uu[j] < ee[j].x && ee[j].y < lam) {
-                        du[j] = S.deg[uu[j]];
-                        dv[j] = S.deg[ee[j].x];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kPU; ++j) {
-                    if (uu[j] < 0 || uu[j] >= ee[j].x) continue;
-                    const long long c = ee[j].y;
-                    const bool ok = c >= lam || (pr_level >= 2 && 2 * c > (du[j] < dv[j] ? du[j] : dv[j]));
-                    if (ok && uf_union(S.par, uu[j], ee[j].x)) ++un;
-                }
-            }
-            if (pr_level >= 2) {
-                for (int u0 = 0; u0 < n; u0 += 32 * kPU) {
-                    int a[kPU], d[kPU];
-                    int2 f0[kPU], f1[kPU];
-#pragma unroll
-                    for (int j = 0; j < kPU; ++j) {
-                        const int u = u0 + 32 * j + lane;
-                        a[j] = d[j] = 0;
-                        if (u < n) {
-                            a[j] = rpA[u];
-                            d[j] = rpA[u + 1] - a[j];
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < kPU; ++j) {
-                        f0[j] = f1[j] = make_int2(0, 0);
-                        if (d[j] == 2) {
-                            f0[j] = adjA[a[j]];
-                            f1[j] = adjA[a[j] + 1];
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < kPU; ++j) {
-                        const int u = u0 + 32 * j + lane;
-                        if (d[j] == 2 && f0[j].y == f1[j].y &&
-                            uf_union(S.par, u, f0[j].x < f1[j].x ? f0[j].x : f1[j].x))
-                            ++un;
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        if (pr_level >= 1)
+            un = chip ? pr_unions(par16, rpA, srcA, adjA, S.deg, n, arcs, lam, pr_level)
+                      : pr_unions(S.par, rpA, srcA, adjA, S.deg, n, arcs, lam, pr_level);
         // one full capped CAPFOREST scan
         ScanArgs A;
         A.g.n = n; A.g.arcs = arcs; A.g.rp = rpA; A.g.src = srcA; A.g.adj = adjA; A.g.deg = S.deg;
@@ -785,7 +1025,7 @@ __device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arc
         const u64 h = splitmix64(seed ^ splitmix64((tag << 20) ^ (u64)round));
         const int start = (int)(h % (u64)n);
         Counters cnt;
-        warp_full_scan<SN>(A, sm, S, n, arcs, lam, start, fifo, cnt);
+        warp_full_scan<SN>(A, sm, S, n, arcs, lam, start, fifo, par16, cnt);
         un += cnt.unions;
         un = warp_sum_ll(un);
         const long long lam2 = ld_volatile_i64(&S.st->lam);
@@ -800,10 +1040,14 @@ __device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arc
         }
         if (un == 0) { err = MC_EINTERNAL; break; }
         // contraction
-        const int nc = warp_relabel(S.par, S.root, S.lab, S.cnt, n);
+        const int nc = chip ? warp_relabel(par16, S.root, S.lab, S.cnt, n) : warp_relabel(S.par, S.root, S.lab, S.cnt, n);
         // the result goes to the B buffers, then A and B swap roles
-        arcs = warp_contract(srcA, adjA, arcs, S.lab, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB, S.deg, S.cnt,
-                             S.mark, &ovf);
+        if (n <= SN)
+            arcs = warp_contract_chip<SN>(srcA, adjA, arcs, S.lab, n, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB,
+                                          S.deg, sm, &ovf);
+        else
+            arcs = warp_contract(srcA, adjA, arcs, S.lab, nc, lam, S.rpT, S.adjT, rpB, srcB, adjB, S.deg, S.cnt,
+                                 S.mark, &ovf);
         for (int v = lane; v < n0; v += 32) S.orig[v] = S.lab[S.orig[v]];
         __syncwarp();
         {
@@ -852,7 +1096,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     constexpr int kCU = 4;
     const int m_raw = __ldg(rp_in + n0);
     const bool rp_on_chip = n0 < SN;
-    int *cur = rp_on_chip ? sm.u.rp : S.cnt;
+    int *cur = rp_on_chip ? sm.u.s.rp : S.cnt;
     for (int v = lane; v <= n0; v += 32) {
         const int r = __ldg(rp_in + v);
         S.rpA[v] = r;
@@ -866,14 +1110,23 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     while (top_row * 2 <= n0 - 1) top_row *= 2;
     bool canon = m_raw >= 0;
     bool sym_ok = true;
+    int vn[kCU], cn[kCU];  // the next chunk's arcs, loaded one chunk ahead
+#pragma unroll
+    for (int j = 0; j < kCU; ++j) {
+        const int i = 32 * j + lane;
+        vn[j] = i < m_raw ? col_in[i] : -1;
+        cn[j] = i < m_raw ? w_in[i] : 0;
+    }
     for (int i0 = 0; i0 < m_raw && canon; i0 += 32 * kCU) {
         int u[kCU], v[kCU], c[kCU];
 #pragma unroll
         for (int j = 0; j < kCU; ++j) {
-            const int i = i0 + 32 * j + lane;
+            const int i = i0 + 32 * j + lane, ia = i + 32 * kCU;
             u[j] = i < m_raw ? 0 : -1;
-            v[j] = i < m_raw ? col_in[i] : -1;
-            c[j] = i < m_raw ? w_in[i] : 0;
+            v[j] = vn[j];
+            c[j] = cn[j];
+            vn[j] = ia < m_raw ? col_in[ia] : -1;
+            cn[j] = ia < m_raw ? w_in[ia] : 0;
         }
         const int prev0 = lane == 0 && i0 > 0 ? col_in[i0 - 1] : -1;
         // row of each arc: the largest u with rps[u] <= i
@@ -986,15 +1239,31 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
 
     long long lam = 0;
     if (!err) {
-        // components
-        for (int v = lane; v < n0; v += 32) S.par[v] = v;
-        __syncwarp();
-        for (long long i = lane; i < arcs; i += 32) {
-            const int u = S.srcA[i], v = S.adjA[i].x;
-            if (u < v) uf_union(S.par, u, v);
+        // components (the union-find on chip when the graph fits)
+        const bool pc = n0 <= SN - 2;
+        unsigned short *p16 = sm.u.s.par;
+        for (int v = lane; v < n0; v += 32) {
+            if (pc) p16[v] = (unsigned short)v;
+            else S.par[v] = v;
         }
         __syncwarp();
-        const int ncomp = warp_relabel(S.par, S.root, S.lab, S.cnt, n0);
+        for (long long i0 = 0; i0 < arcs; i0 += 128) {
+            int uu[4], vv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long i = i0 + 32 * j + lane;
+                uu[j] = vv[j] = 0;
+                if (i < arcs) {
+                    uu[j] = S.srcA[i];
+                    vv[j] = S.adjA[i].x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (uu[j] < vv[j]) (void)(pc ? wuf_union(p16, uu[j], vv[j]) : wuf_union(S.par, uu[j], vv[j]));
+        }
+        __syncwarp();
+        const int ncomp = pc ? warp_relabel(p16, S.root, S.lab, S.cnt, n0) : warp_relabel(S.par, S.root, S.lab, S.cnt, n0);
         if (ncomp > 1) {
             const int r0 = S.root[0];
             warp_side_bits(S.best, n0, [&](int v) { return S.root[v] != r0; });
