@@ -1106,8 +1106,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     for (int v = lane; v < n0; v += 32) S.deg[v] = 0;
     __syncwarp();
     const int *rps = rp_on_chip ? sm.r : rp_in;
-    int top_row = 1;  // the largest power of two <= n0 - 1 (n0 >= 2)
-    while (top_row * 2 <= n0 - 1) top_row *= 2;
+    int ucur = 0;  // a row starting at or before the window's first arc
     bool canon = m_raw >= 0;
     bool sym_ok = true;
     int vn[kCU], cn[kCU];  // the next chunk's arcs, loaded one chunk ahead
@@ -1129,13 +1128,36 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
             cn[j] = ia < m_raw ? w_in[ia] : 0;
         }
         const int prev0 = lane == 0 && i0 > 0 ? col_in[i0 - 1] : -1;
-        // row of each arc: the largest u with rps[u] <= i
-        for (int step = top_row; step > 0; step >>= 1) {
+        // row of each arc: ucur plus the row starts in (ucur, i], counted
+        // against 32 consecutive starts held one a lane (a 5-step search over
+        // shuffles), 32 more while some arc lies past them
+        {
+            int base = ucur;
+            unsigned pending = 0u;
 #pragma unroll
-            for (int j = 0; j < kCU; ++j) {
-                const int i = i0 + 32 * j + lane;
-                if (u[j] >= 0 && u[j] + step <= n0 - 1 && rps[u[j] + step] <= i) u[j] += step;
+            for (int j = 0; j < kCU; ++j)
+                if (u[j] >= 0) pending |= 1u << j;
+            while (__any_sync(0xffffffffu, pending != 0u)) {
+                const int su = base + 1 + lane;
+                const int st = su <= n0 ? rps[su] : INT_MAX;
+                const int st31 = __shfl_sync(0xffffffffu, st, 31);
+#pragma unroll
+                for (int j = 0; j < kCU; ++j) {
+                    const int i = i0 + 32 * j + lane;
+                    int pos = 0;  // starts at or before i among the first 31
+#pragma unroll
+                    for (int b = 16; b > 0; b >>= 1)
+                        if (__shfl_sync(0xffffffffu, st, pos + b - 1) <= i) pos += b;
+                    if (pos == 31 && st31 <= i) pos = 32;
+                    if (((pending >> j) & 1u) && pos < 32) {
+                        u[j] = base + pos;
+                        pending &= ~(1u << j);
+                    }
+                }
+                base += 32;
             }
+            const int lastu = __shfl_sync(0xffffffffu, u[kCU - 1], 31);
+            if (lastu >= 0) ucur = lastu;
         }
         bool ok = true;
 #pragma unroll
