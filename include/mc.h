@@ -230,6 +230,21 @@ int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
                       const mc_options *opt, int32_t *best_shape, double *ms_per_shape,
                       int32_t max_shapes);
 
+/*
+ * mc_batch_shape_count -- how many batched-kernel shapes mc_batch_autotune
+ * chooses from (the valid indices are 0 .. count - 1).  No paper counterpart.
+ */
+int mc_batch_shape_count(void);
+
+/*
+ * mc_batch_set_shape -- choose the batched-kernel shape for later
+ * mc_batch_min_cut calls of this process, as mc_batch_autotune does after
+ * timing them; -1 returns to the default shape.  Every shape gives the same
+ * lambdas; only the time differs.  No paper counterpart.  Returns MC_EINVAL
+ * for an index outside -1 .. mc_batch_shape_count() - 1, else MC_OK.
+ */
+int mc_batch_set_shape(int32_t shape);
+
 /* Message for an error code (thread-local detail for MC_ECUDA). */
 const char *mc_strerror(int code);
 

@@ -10,10 +10,11 @@ Python side: :mod:`paper_1808_05458_gb300.mincut` (ctypes binding).
 from .mincut import (MC_BOUND_BEST, MC_BOUND_DEGREE, MC_BOUND_LEARNED, MC_BOUND_LP, MC_EINVAL,
                      MC_ENOMEM, MC_EOVERFLOW, MC_OK, MC_PQ_FIFO, MC_PQ_LIFO, PROPOSER_PARAMS, Graph, MinCut,
                      MinCutError, Proposer,
-                     batch_autotune, batch_min_cut, bitmap_to_side, load_library, min_cut,
+                     batch_autotune, batch_min_cut, batch_set_shape, batch_shape_count, bitmap_to_side, load_library, min_cut,
                      options, strerror, test_fail_alloc_after)
 
 __all__ = ["Graph", "MinCut", "MinCutError", "min_cut", "batch_min_cut", "batch_autotune",
+           "batch_set_shape", "batch_shape_count",
            "options", "strerror", "Proposer", "PROPOSER_PARAMS", "MC_BOUND_LEARNED",
            "MC_BOUND_BEST",
            "load_library", "bitmap_to_side", "MC_PQ_LIFO", "MC_PQ_FIFO", "MC_BOUND_DEGREE",

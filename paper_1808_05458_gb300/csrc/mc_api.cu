@@ -768,6 +768,14 @@ int mc_batch_autotune(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
     return MC_OK;
 }
 
+int mc_batch_shape_count(void) { return batch_shapes(); }
+
+int mc_batch_set_shape(int32_t shape) {
+    if (shape < -1 || shape >= batch_shapes()) return MC_EINVAL;
+    batch_set_shape(shape);
+    return MC_OK;
+}
+
 int mc_proposer_create(const float *params, uint64_t seed, mc_proposer **out) {
     if (!out) return MC_EINVAL;
     const int P = proposer_nparams();

@@ -73,7 +73,7 @@ EXPORTS = ("mc_options_default", "mc_graph_create", "mc_graph_destroy", "mc_grap
            "mc_batch_autotune", "mc_proposer_create", "mc_proposer_destroy", "mc_proposer_get",
            "mc_proposer_set", "mc_proposer_forward", "mc_proposer_grad", "mc_proposer_train_step",
            "mc_proposer_bound", "mc_test_fail_alloc_after", "mc_graph_coarsen",
-           "mc_step_capforest_range")
+           "mc_step_capforest_range", "mc_batch_shape_count", "mc_batch_set_shape")
 
 
 def library_path() -> str:
@@ -99,6 +99,8 @@ def load_library():
     lib.mc_min_cut.argtypes = [vp, P(McOptions), P(i64), vp, P(McStats)]
     lib.mc_batch_min_cut.argtypes = [i32, vp, vp, vp, vp, vp, P(McOptions), vp, vp, vp, P(McStats)]
     lib.mc_test_fail_alloc_after.argtypes = [i64]
+    lib.mc_batch_shape_count.argtypes = []
+    lib.mc_batch_set_shape.argtypes = [i32]
     lib.mc_strerror.argtypes = [ctypes.c_int]
     lib.mc_strerror.restype = ctypes.c_char_p
     lib.mc_graph_export.argtypes = [vp, vp, vp, vp]
@@ -457,6 +459,17 @@ def min_cut(row_ptr, col, w, **opt) -> MinCut:
     """One-shot: create, solve, destroy."""
     with Graph(row_ptr, col, w) as g:
         return g.min_cut(options(**opt))
+
+
+def batch_shape_count() -> int:
+    """How many batched-kernel shapes the autotuner chooses from."""
+    return int(load_library().mc_batch_shape_count())
+
+
+def batch_set_shape(shape: int) -> None:
+    """Use batched-kernel shape `shape` (0 .. batch_shape_count() - 1; -1 =
+    the default) for later batch_min_cut calls, as batch_autotune does."""
+    _check(load_library().mc_batch_set_shape(int(shape)), "mc_batch_set_shape")
 
 
 def batch_autotune(row_ptr, col, w, vtx_off, arc_off, opts: McOptions | None = None):

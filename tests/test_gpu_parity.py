@@ -747,6 +747,42 @@ def test_batch_every_shape_and_autotune(mc):
     assert (lam == ref).all()
 
 
+def _reverse_rows(g):
+    rp, col, w = (np.array(a) for a in g)
+    for v in range(len(rp) - 1):
+        col[rp[v]:rp[v + 1]] = col[rp[v]:rp[v + 1]][::-1].copy()
+        w[rp[v]:rp[v + 1]] = w[rp[v]:rp[v + 1]][::-1].copy()
+    return rp, col, w
+
+
+def test_batch_every_shape_exact_at_size_boundaries(mc):
+    # each kernel shape (shared vertices per warp 512, 1024 or 2048) on graphs
+    # just below, at and above those sizes and the 16-bit union-find's limit
+    # (SN - 2): on-chip and global paths alike; caps of 2^25 and above take
+    # the bucket-list scan; reversed rows take the general canonicalisation
+    sizes = (2, 3, 33, 65, 254, 255, 256, 257, 510, 511, 512, 513, 1022, 1023, 1024, 1025,
+             2046, 2047, 2048, 2049)
+    graphs = [graphgen.random_connected(n, 2 * n, seed=300 + i, wmax=100) for i, n in enumerate(sizes)]
+    heavy = graphgen.random_connected(300, 600, seed=7, wmax=100)
+    graphs.append((heavy[0], heavy[1], ((heavy[2].astype(np.int64) + 128) << 18).astype(np.int32)))
+    graphs.append(_reverse_rows(graphgen.random_connected(700, 1400, seed=8, wmax=100)))
+    graphs.append(_reverse_rows(graphgen.random_connected(1023, 2000, seed=9, wmax=100)))
+    graphs.append(graphgen.two_cliques(40, 3, seed=5))
+    b = _concat(graphs)
+    ref = [oracle.noi(*g)[0] for g in graphs]
+    try:
+        for k in range(mc.batch_shape_count()):
+            mc.batch_set_shape(k)
+            for order in (mc.MC_PQ_LIFO, mc.MC_PQ_FIFO):
+                lam, bits, boff, _ = mc.batch_min_cut(*b, mc.options(pq_order=order), bitmaps=True)
+                assert list(lam) == ref, (k, order, [(i, lam[i], ref[i]) for i in range(len(ref)) if lam[i] != ref[i]])
+                _check_batch_sides(b, lam, bits, boff, range(len(graphs)))
+        with pytest.raises(mc.MinCutError):
+            mc.batch_set_shape(mc.batch_shape_count())
+    finally:
+        mc.batch_set_shape(-1)
+
+
 # ------------------------------------------------------------ full sizes --
 def test_rhg_2_20_full_size(mc):
     # the plain-path workload: RHG n = 2^20, average degree 32, exponent 5
