@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "mc_internal.cuh"
+#include "mc_sort.cuh"
 
 namespace mc {
 
@@ -370,11 +371,13 @@ __global__ void k_rs_hist(const u64 *__restrict__ keys, i64 n, int shift, int nt
     hist[(i64)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// VALS: an int32 value travels with each key (else keys only)
+template <bool VALS>
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__restrict__ kout,
              int *__restrict__ vout, i64 n, int shift, int ntiles, const int *__restrict__ offs) {
     __shared__ u64 sk[kRsTile];
-    __shared__ int sv[kRsTile];
+    __shared__ int sv[VALS ? kRsTile : 1];
     __shared__ int wcnt[kRsWarps][256];
     __shared__ int dstart[256];
     __shared__ int gofs[256];
@@ -396,7 +399,7 @@ k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__re
         i64 i = tile0 + li;
         bool ok = li < count;
         key[j] = ok ? kin[i] : ~0ULL;
-        val[j] = ok ? vin[i] : 0;
+        val[j] = VALS && ok ? vin[i] : 0;
         dig[j] = ok ? (int)((key[j] >> shift) & 255) : 255;
     }
 #pragma unroll
@@ -428,7 +431,7 @@ k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__re
     for (int j = 0; j < kRsItems; ++j) {
         int pos = dstart[dig[j]] + wcnt[wid][dig[j]] + rank[j];
         sk[pos] = key[j];
-        sv[pos] = val[j];
+        if (VALS) sv[pos] = val[j];
     }
     __syncthreads();
     for (int p = threadIdx.x; p < count; p += kRsThreads) {
@@ -436,7 +439,7 @@ k_rs_scatter(const u64 *__restrict__ kin, const int *__restrict__ vin, u64 *__re
         int d = (int)((k >> shift) & 255);
         i64 o = (i64)gofs[d] + (p - dstart[d]);
         kout[o] = k;
-        vout[o] = sv[p];
+        if (VALS) vout[o] = sv[p];
     }
 }
 
@@ -453,10 +456,29 @@ int radix_sort_pairs(u64 *keysA, int *valsA, u64 *keysB, int *valsB, i64 n, int 
     for (int shift = 0; shift < bits; shift += 8) {
         ++::mc::g_launches; k_rs_hist<<<ntiles, kRsThreads, 0, s>>>(ki, n, shift, ntiles, hist);
         MC_TRY(exclusive_scan_i32(hist, hist, (i64)256 * ntiles, nullptr, scan_tmp, err, s));
-        ++::mc::g_launches; k_rs_scatter<<<ntiles, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, hist);
+        ++::mc::g_launches; k_rs_scatter<true><<<ntiles, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, hist);
         MC_CUDA(cudaGetLastError());
         u64 *tk = ki; ki = ko; ko = tk;
         int *tv = vi; vi = vo; vo = tv;
+        *in_b = !*in_b;
+    }
+    return MC_OK;
+}
+
+int radix_sort_keys(u64 *keysA, u64 *keysB, i64 n, int shift0, int bits, u32 *tmp, int *scan_tmp, int *err,
+                    bool *in_b, cudaStream_t s) {
+    *in_b = false;
+    if (n <= 1 || bits <= 0) return MC_OK;
+    const int ntiles = div_up(n, kRsTile);
+    int *hist = reinterpret_cast<int *>(tmp);
+    u64 *ki = keysA, *ko = keysB;
+    for (int shift = shift0; shift < shift0 + bits; shift += 8) {
+        ++::mc::g_launches; k_rs_hist<<<ntiles, kRsThreads, 0, s>>>(ki, n, shift, ntiles, hist);
+        MC_TRY(exclusive_scan_i32(hist, hist, (i64)256 * ntiles, nullptr, scan_tmp, err, s));
+        ++::mc::g_launches; k_rs_scatter<false><<<ntiles, kRsThreads, 0, s>>>(ki, nullptr, ko, nullptr, n, shift,
+                                                                            ntiles, hist);
+        MC_CUDA(cudaGetLastError());
+        u64 *tk = ki; ki = ko; ko = tk;
         *in_b = !*in_b;
     }
     return MC_OK;
