@@ -193,7 +193,7 @@ def run_reference(args, rank, world):
 
 def form_batched(mc, peak, seed=1):
     """The batched form (4096 graphs, n in 50..2000, degree 4..16, weights
-    1..100): one mc_batch_min_cut per step through the C ABI from host
+    1..100): one mc_batch_min_cut per step through the C ABI from pinned host
     arrays (H2D of the batch, one persistent launch, D2H of the lambdas and
     side bitmaps), every lambda checked against the oracle's lambdas stored
     in tests/golden/batch_lambdas_seed1.json (written by the script beside
@@ -209,6 +209,11 @@ def form_batched(mc, peak, seed=1):
         h.update(a.tobytes())
     assert h.hexdigest()[:16] == stored["arrays_sha256_16"], "batch generator output changed"
     ref = np.array(stored["lambdas"], dtype=np.int64)
+    # the batch's host arrays in pinned memory, as a serving process keeps
+    # its staging buffers (the timed region copies them to the device)
+    import torch
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in b]
+    b = tuple(t.numpy() for t in pinned)
     mc.batch_autotune(*b)
     for _ in range(2):
         lam, _, _, st = mc.batch_min_cut(*b, bitmaps=True)

@@ -208,8 +208,10 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,
  * (u, v, c) has its mirror (v, u, c)), which the kernel checks per graph; a
  * disconnected graph gets lambda 0.  stats: n_input/m_input are totals,
  * ms_total is the kernel's device time.
- * Errors: MC_EINVAL (n_g < 2, bad offsets, neighbour out of range, negative
- * weight, an arc without its mirror), MC_EOVERFLOW, MC_ENOMEM, MC_ECUDA,
+ * Errors: MC_EINVAL (n_g < 2, bad offsets -- a graph's first offset not 0 or
+ * its last not its arc count, refused before any launch, or an offset below
+ * its predecessor, found by the kernel before it reads that graph's arcs --,
+ * neighbour out of range, negative weight, an arc without its mirror), MC_EOVERFLOW, MC_ENOMEM, MC_ECUDA,
  * MC_EINTERNAL -- the first failing graph's code.
  */
 int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,

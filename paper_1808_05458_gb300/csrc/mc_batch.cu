@@ -1097,17 +1097,31 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
     const int m_raw = __ldg(rp_in + n0);
     const bool rp_on_chip = n0 < SN;
     int *cur = rp_on_chip ? sm.u.s.rp : S.cnt;
-    for (int v = lane; v <= n0; v += 32) {
-        const int r = __ldg(rp_in + v);
-        S.rpA[v] = r;
-        if (rp_on_chip) sm.r[v] = r;
-        if (v > 0) cur[v - 1] = r;  // no entry above v-1 seen yet: the row's end
+    // staged, and checked: offsets from 0 to the arc count, never falling
+    // (the host checked the ends; a falling offset makes the graph MC_EINVAL
+    // before any of its arcs is read)
+    bool rp_bad = false;
+    int rprev = 0;  // the offset before this chunk
+    for (int v0 = 0; v0 <= n0; v0 += 32) {
+        const int v = v0 + lane;
+        const int r = v <= n0 ? __ldg(rp_in + v) : INT_MAX;
+        int pr = __shfl_up_sync(0xffffffffu, r, 1);
+        if (lane == 0) pr = rprev;
+        if (v <= n0) {
+            if (r < pr || (v == 0 && r != 0) || (v == n0 && r != m_raw)) rp_bad = true;
+            S.rpA[v] = r;
+            if (rp_on_chip) sm.r[v] = r;
+            if (v > 0) cur[v - 1] = r;  // no entry above v-1 seen yet: the row's end
+        }
+        rprev = __shfl_sync(0xffffffffu, r, 31);
     }
+    const bool rp_ok = !__any_sync(0xffffffffu, rp_bad);  // warp-uniform
+    if (!rp_ok) err = MC_EINVAL;
     for (int v = lane; v < n0; v += 32) S.deg[v] = 0;
     __syncwarp();
     const int *rps = rp_on_chip ? sm.r : rp_in;
     int ucur = 0;  // a row starting at or before the window's first arc
-    bool canon = m_raw >= 0;
+    bool canon = m_raw >= 0 && rp_ok;
     bool sym_ok = true;
     int vn[kCU], cn[kCU];  // the next chunk's arcs, loaded one chunk ahead
 #pragma unroll
@@ -1221,7 +1235,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
 
     // raw arcs -> (srcB, adjB), dropping self-loops and zero weights
     long long m = 0;
-    for (int u = 0; u < n0 && !canon; ++u) {
+    for (int u = 0; u < n0 && !canon && rp_ok; ++u) {
         const int lo = rp_in[u], hi = rp_in[u + 1];
         for (int e0 = lo; e0 < hi; e0 += 32) {
             const int e = e0 + lane;
@@ -1244,7 +1258,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
         }
     }
     err = __reduce_or_sync(0xffffffffu, err);
-    if (!canon) {
+    if (!canon && !err) {
         // canonical CSR in A (identity labels)
         for (int v = lane; v < n0; v += 32) S.lab[v] = v;
         __syncwarp();
@@ -1461,9 +1475,8 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
         const long long a = arc_off[k + 1] - arc_off[k];
         if (n < 2 || n > (1 << 24) || a < 0) return MC_EINVAL;
         const int *rp = row_ptr + vtx_off[k] + k;
+        // the ends here; a falling offset inside is found by the kernel
         if (rp[0] != 0 || (long long)rp[n] != a) return MC_EINVAL;
-        for (long long v = 0; v < n; ++v)
-            if (rp[v + 1] < rp[v]) return MC_EINVAL;
         nmax = std::max(nmax, (int)n);
         amax = std::max(amax, a);
     }

@@ -680,6 +680,14 @@ def test_batch_invalid(mc):
     b = _concat([(rp, col, -w)])
     with pytest.raises(mc.MinCutError):
         mc.batch_min_cut(*b)
+    # a row offset that falls (the ends right): refused before any arc is read
+    good = graphgen.complete(5, 2)
+    rp_f = rp.copy()
+    rp_f[2] = rp_f[1] - 1
+    for graphs in ([(rp_f, col, w)], [good, (rp_f, col, w), good]):
+        with pytest.raises(mc.MinCutError) as ei:
+            mc.batch_min_cut(*_concat(graphs))
+        assert ei.value.code == mc.MC_EINVAL
 
 
 def test_batch_asymmetric_rejected(mc):
