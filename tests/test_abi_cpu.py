@@ -59,6 +59,11 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.mc_graph_create(1, rp.ctypes.data, None, None, 0, ctypes.byref(h)) == -1
     assert lib.mc_min_cut(None, None, None, None, None) == -1
     assert lib.mc_graph_destroy(None) == -1
+    # the batched-kernel shape selector: indices -1 .. count - 1 only
+    count = lib.mc_batch_shape_count()
+    assert count >= 1
+    assert lib.mc_batch_set_shape(count) == -1 and lib.mc_batch_set_shape(-2) == -1
+    assert lib.mc_batch_set_shape(count - 1) == 0 and lib.mc_batch_set_shape(-1) == 0
 
 
 def test_binding_struct_layouts_match_header(tmp_path):
