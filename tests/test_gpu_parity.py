@@ -791,6 +791,49 @@ def test_batch_every_shape_exact_at_size_boundaries(mc):
         mc.batch_set_shape(-1)
 
 
+def test_batch_random_kinds_every_shape(mc):
+    # mixed kinds per shape: dense graphs (contracted rows far past 32 arcs),
+    # sparse and disconnected ones, raw edge lists with loops, repeats and
+    # zero weights, heavy weights, and cliques joined by a few edges
+    rng = np.random.default_rng(77)
+    graphs = []
+    for i in range(120):
+        kind = i % 6
+        if kind == 0:
+            n = int(rng.integers(40, 260))
+            g = graphgen.random_gnp(n, float(rng.uniform(0.2, 0.6)), seed=500 + i, wmax=int(rng.integers(1, 50)))
+        elif kind == 1:
+            n = int(rng.integers(100, 2100))
+            g = graphgen.random_connected(n, int(rng.integers(n, 6 * n)), seed=500 + i, wmax=100)
+        elif kind == 2:
+            n = int(rng.integers(20, 400))
+            g = graphgen.random_gnp(n, float(rng.uniform(0.002, 0.02)), seed=500 + i, wmax=10)
+        elif kind == 3:
+            n = int(rng.integers(10, 900))
+            m = int(rng.integers(n, 8 * n))
+            g = graphgen.from_edges(n, rng.integers(0, n, size=m), rng.integers(0, n, size=m),
+                                    rng.integers(0, 5, size=m))
+        elif kind == 4:
+            n = int(rng.integers(50, 1500))
+            g0 = graphgen.random_connected(n, 3 * n, seed=500 + i, wmax=100)
+            g = (g0[0], g0[1], ((g0[2].astype(np.int64) + 128) << 17).astype(np.int32))
+        else:
+            g = graphgen.two_cliques(int(rng.integers(10, 60)), int(rng.integers(1, 6)), seed=500 + i)
+        if len(g[0]) - 1 >= 2:
+            graphs.append(g)
+    b = _concat(graphs)
+    ref = [oracle.noi(*g)[0] for g in graphs]
+    try:
+        for k in range(mc.batch_shape_count()):
+            mc.batch_set_shape(k)
+            lam, bits, boff, _ = mc.batch_min_cut(*b, bitmaps=True)
+            bad = [(i, lam[i], ref[i]) for i in range(len(ref)) if lam[i] != ref[i]]
+            assert not bad, (k, bad[:5])
+            _check_batch_sides(b, lam, bits, boff, [i for i in range(len(graphs)) if ref[i] > 0])
+    finally:
+        mc.batch_set_shape(-1)
+
+
 # ------------------------------------------------------------ full sizes --
 def test_rhg_2_20_full_size(mc):
     # the plain-path workload: RHG n = 2^20, average degree 32, exponent 5
