@@ -1083,9 +1083,9 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
 
     // Input that is canonical as given (rows strictly increasing, no
     // self-loop, positive weights, neighbours in range) is copied into A in
-    // one arc-parallel pass: each arc's row by binary search in the offsets
-    // (staged on chip when they fit), the degrees by a segmented sum over
-    // the lanes of a row.  The same pass checks symmetry in row order: the
+    // one arc-parallel pass: each arc's row counted against 32 consecutive
+    // row starts held one a lane (the offsets staged on chip when they fit),
+    // the degrees by a segmented sum over the lanes of a row.  The same pass checks symmetry in row order: the
     // downward arcs (u -> v, v < u) that reach v, met in increasing u, must
     // match the entries of row v above v one by one (a cursor per row,
     // starting at the row's first entry above v), with equal weights, and
@@ -1108,7 +1108,7 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
         int pr = __shfl_up_sync(0xffffffffu, r, 1);
         if (lane == 0) pr = rprev;
         if (v <= n0) {
-            if (r < pr || (v == 0 && r != 0) || (v == n0 && r != m_raw)) rp_bad = true;
+            if (r < pr || (v == 0 && r != 0)) rp_bad = true;
             S.rpA[v] = r;
             if (rp_on_chip) sm.r[v] = r;
             if (v > 0) cur[v - 1] = r;  // no entry above v-1 seen yet: the row's end
