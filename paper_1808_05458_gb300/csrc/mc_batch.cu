@@ -1275,44 +1275,16 @@ __device__ void solve_one(const BatchIn &B, int gi, Scratch &S, WarpSmem<SN> &sm
 
     long long lam = 0;
     if (!err) {
-        // components (the union-find on chip when the graph fits)
-        const bool pc = n0 <= SN - 2;
-        unsigned short *p16 = sm.u.s.par;
-        for (int v = lane; v < n0; v += 32) {
-            if (pc) p16[v] = (unsigned short)v;
-            else S.par[v] = v;
-        }
+        // no separate components pass: a disconnected graph's first scan
+        // ends with its start's component, whose cut (alpha = 0) sets
+        // lambda = 0 and the side; a vertex without arcs gives delta = 0
+        int arg = 0;
+        warp_min_deg(S.deg, n0, &lam, &arg);
+        if (lam >= 0x7FFFFFFD) err = MC_EOVERFLOW;
+        warp_side_bits(S.best, n0, [&](int v) { return v == arg; });
+        for (int v = lane; v < n0; v += 32) S.orig[v] = v;
         __syncwarp();
-        for (long long i0 = 0; i0 < arcs; i0 += 128) {
-            int uu[4], vv[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const long long i = i0 + 32 * j + lane;
-                uu[j] = vv[j] = 0;
-                if (i < arcs) {
-                    uu[j] = S.srcA[i];
-                    vv[j] = S.adjA[i].x;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (uu[j] < vv[j]) (void)(pc ? wuf_union(p16, uu[j], vv[j]) : wuf_union(S.par, uu[j], vv[j]));
-        }
-        __syncwarp();
-        const int ncomp = pc ? warp_relabel(p16, S.root, S.lab, S.cnt, n0) : warp_relabel(S.par, S.root, S.lab, S.cnt, n0);
-        if (ncomp > 1) {
-            const int r0 = S.root[0];
-            warp_side_bits(S.best, n0, [&](int v) { return S.root[v] != r0; });
-            lam = 0;
-        } else {
-            int arg = 0;
-            warp_min_deg(S.deg, n0, &lam, &arg);
-            if (lam >= 0x7FFFFFFD) err = MC_EOVERFLOW;
-            warp_side_bits(S.best, n0, [&](int v) { return v == arg; });
-            for (int v = lane; v < n0; v += 32) S.orig[v] = v;
-            __syncwarp();
-            exact_rounds<SN>(S, sm, n0, arcs, lam, err, ovf, B.seed, (u64)gi, B.pr_level, B.fifo);
-        }
+        exact_rounds<SN>(S, sm, n0, arcs, lam, err, ovf, B.seed, (u64)gi, B.pr_level, B.fifo);
     }
     if (lane == 0) {
         B.lam_out[gi] = lam;
