@@ -1007,16 +1007,18 @@ __device__ void exact_rounds(Scratch &S, WarpSmem<SN> &sm, int n0, long long arc
         if (++guard > 4 * n0 + 16) { err = MC_EINTERNAL; break; }
         const bool chip = round_on_chip<SN>(n, lam, fifo);
         unsigned short *par16 = chip ? sm.u.s.par : nullptr;
-        for (int v = lane; v < n; v += 32) {
-            if (chip) par16[v] = (unsigned short)v;
-            else S.par[v] = v;
-        }
+        // on chip the PR unions run on 32-bit parents in r (idle until the
+        // scan), then pass to the 16-bit parents the scan's joins extend
+        int *par32 = chip ? sm.r : S.par;
+        for (int v = lane; v < n; v += 32) par32[v] = v;
         __syncwarp();
         long long un = 0;
         // Padberg-Rinaldi PR1/PR2 and the degree-2 tie rule
-        if (pr_level >= 1)
-            un = chip ? pr_unions(par16, rpA, srcA, adjA, S.deg, n, arcs, lam, pr_level)
-                      : pr_unions(S.par, rpA, srcA, adjA, S.deg, n, arcs, lam, pr_level);
+        if (pr_level >= 1) un = pr_unions(par32, rpA, srcA, adjA, S.deg, n, arcs, lam, pr_level);
+        if (chip) {
+            for (int v = lane; v < n; v += 32) par16[v] = (unsigned short)par32[v];
+            __syncwarp();
+        }
         // one full capped CAPFOREST scan
         ScanArgs A;
         A.g.n = n; A.g.arcs = arcs; A.g.rp = rpA; A.g.src = srcA; A.g.adj = adjA; A.g.deg = S.deg;
