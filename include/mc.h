@@ -202,7 +202,8 @@ int mc_min_cut(mc_graph *g, const mc_options *opt, int64_t *lambda_out,
  *             start at bitmap_word_off[g] (host)
  *   bitmap_word_off  G+1 int64, required when bitmaps is non-NULL
  * One kernel launch solves the whole batch: one warp per graph, graphs
- * taken largest first (Alg. 2 per graph with full capped scans, PR1/PR2 and
+ * taken largest first (Alg. 2 per graph with full capped scans, PR1/PR2 when
+ * opt->pr_level >= 1 and the kernel shape in use runs them, and
  * in-warp contraction).  Self-loops and zero weights are dropped and
  * parallel arcs merged; after that every graph must be symmetric (each arc
  * (u, v, c) has its mirror (v, u, c)), which the kernel checks per graph; a
@@ -221,7 +222,8 @@ int mc_batch_min_cut(int32_t G, const int64_t *vtx_off, const int64_t *arc_off,
 
 /*
  * mc_batch_autotune -- time every batched-kernel shape (warps per block x
- * vertices whose scan state fits in shared memory per warp) on this batch,
+ * vertices whose scan state fits in shared memory per warp x whether the
+ * in-warp PR1/PR2 tests run, which never changes a lambda) on this batch,
  * keep the fastest for later mc_batch_min_cut calls on the current device
  * of this process, and report it.  Arguments as mc_batch_min_cut;
  * ms_per_shape (max_shapes entries, may be NULL) receives each shape's

@@ -1402,10 +1402,16 @@ int launch_batch(const BatchIn &B, int warps, cudaStream_t s) {
 
 // batch configurations the autotuner chooses from: warps per block x shared
 // vertices per warp
+// and whether the in-warp PR1/PR2 tests run (they never change a lambda;
+// on small graphs the scans' own joins often make them cost more than they
+// save, so the autotuner times both)
 struct BatchShape {
     int wpb, sn;
+    bool pr;
 };
-static const BatchShape kShapes[] = {{4, 1024}, {4, 2048}, {8, 512}, {8, 1024}, {2, 2048}};
+static const BatchShape kShapes[] = {{4, 1024, true},  {4, 2048, true},  {8, 512, true},  {8, 1024, true},
+                                     {2, 2048, true},  {4, 1024, false}, {4, 2048, false}, {8, 512, false},
+                                     {8, 1024, false}, {2, 2048, false}};
 static int g_shape_choice = -1;  // -1: not tuned
 
 static int run_batch(int shape, BatchIn B, int warps, cudaStream_t s) {
@@ -1507,7 +1513,7 @@ int batch_solve(int G, const long long *vtx_off, const long long *arc_off, const
     B.scratch = ctx.scratch;
     B.L = L;
     B.seed = o.seed;
-    B.pr_level = o.pr_level;
+    B.pr_level = kShapes[shape].pr ? o.pr_level : 0;
     B.fifo = o.pq_order == MC_PQ_FIFO;
 
     cudaEvent_t ea, eb;
